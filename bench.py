@@ -1,0 +1,503 @@
+#!/usr/bin/env python
+"""Throughput of the spherical-harmonics hot path on GB300.
+
+Step = one forward pass (values + Cartesian gradients, FP32, l_max = 8) over
+N = 4,194,304 synthetic points (directions uniform on the sphere, radii
+~ U[0.5, 5.0]), written as sph [N, 81] and dsph [N, 3, 81]: 5.49 GB of output
+per step. Metric: points/s, with the dominant kernel's achieved HBM bandwidth
+against the measured copy bandwidth.
+
+Also reported (separate keys): the fused recompute-backward against the
+materialise-then-contract backward (N = 4,194,304 edge vectors, |r| ~ U[0.7, 6],
+l_max = 6, upstream g ~ N(0,1)), both with their error against the FP64
+oracle on sampled points; the double backward; the end-to-end throughput from
+pinned host memory; and the FP64 oracle timed on the host cores.
+
+Multi-GPU: one process per GPU (torchrun); each rank evaluates its own N
+points (weak scaling, no collective on the data path); timing is the max
+over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "points/s, Y_lm + grad FP32 l_max=8 (forward values+Cartesian gradients)"
+N_POINTS = 4_194_304
+L_MAX = 8
+BWD_N = 4_194_304
+BWD_L = 6
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+# ---------------------------------------------------------------- CPU (oracle)
+def _oracle_chunk(args):
+    n, seed, l_max = args
+    import numpy as np
+
+    import oracle
+    from paper_2302_08381_gb300 import inputs
+
+    xyz = inputs.shell_points(n, 0.5, 5.0, seed=seed).astype(np.float64)
+    v, g = oracle.spherical_harmonics_grad(xyz, l_max, False)
+    return float(v.sum() + g.sum())
+
+
+def time_oracle(total_points: int, l_max: int, chunk: int = 16384):
+    """Times the FP64 oracle (values + gradients) over total_points on all host
+    cores with a spawn pool. Returns (points/s, cores, seconds)."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    nchunks = max(1, total_points // chunk)
+    work = [(chunk, 1000 + i, l_max) for i in range(nchunks)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(256, 1, l_max)] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_chunk, work, chunksize=1)
+        dt = time.perf_counter() - t0
+    return nchunks * chunk / dt, cores, dt
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+            self.t0 = time.time()
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(
+                    {
+                        "sm": float(parts[1]),
+                        "max": float(parts[2]),
+                        "power": float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else None,
+                        "hw_slowdown": parts[5] == "Active",
+                        "hw_thermal_slowdown": parts[6] == "Active",
+                        "sw_thermal_slowdown": parts[7] == "Active",
+                        "sw_power_cap": parts[8] == "Active",
+                    }
+                )
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["power"] is None or r["power"] > 300] or rows
+        reasons = sorted(
+            {k for r in loaded for k in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap") if r[k]}
+        )
+        return {
+            "sm_mhz": statistics.median(r["sm"] for r in loaded),
+            "sm_max_mhz": max(r["max"] for r in rows),
+            "reasons": reasons,
+            "samples": len(rows),
+            "samples_under_load": len(loaded),
+        }
+
+
+def physical_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_tag: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    ent = rec.get(kernel_tag)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_08381_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    if ent.get("sources_sha256") != h.hexdigest():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sample = 131_072
+    cores = os.cpu_count() or 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        vps, cores, dt = time_oracle(sample, L_MAX)
+        if i >= args.warmup:
+            times.append(dt)
+    step = statistics.median(times)
+    value = sample / step
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "forward values+gradients l_max=8, FP64 oracle on a sample", "points_per_step": sample},
+        "cpu_baseline": {
+            "value": value,
+            "unit": "points/s",
+            "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sample} points per step of the benchmark distribution, spawn pool of {cores} processes",
+        },
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    # CPU baseline first: the spawn pool is created before any CUDA call.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.no_extras:
+        sample = 1_048_576
+        vps, cores, dt = time_oracle(sample, L_MAX)
+        cpu = {
+            "value": vps,
+            "unit": "points/s",
+            "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sample} points of the benchmark distribution, l_max=8 values+gradients, FP64, "
+            f"spawn pool of {cores} processes ({dt:.1f} s)",
+        }
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_08381_gb300 import _capi, api, inputs
+    from paper_2302_08381_gb300 import build as _build
+
+    if not os.path.exists(_capi.LIB_PATH):
+        _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, L = args.n, L_MAX
+    K = (L + 1) ** 2
+    xyz_np = inputs.shell_points(n, 0.5, 5.0, seed=8 + rank)
+    xyz = torch.from_numpy(xyz_np).to(dev)
+    sph = torch.empty((n, K), device=dev)
+    dsph = torch.empty((n, 3, K), device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.spherical_harmonics(xyz, L, False, gradients=True, out=(sph, dsph))
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(physical_gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed launches (outside the events)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    # Keep the GPU under the same load a little longer for clock samples.
+    t_extra = time.perf_counter()
+    while time.perf_counter() - t_extra < 1.0:
+        for _ in range(20):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+    clocks = sampler.stop()
+
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    kernel_ms = sum(per) / len(per)
+    t_max = torch.tensor([kernel_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = world * n / (ms * 1e-3)
+
+    bytes_per_launch = n * (3 * 4 + K * 4 * 4)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / (ms * 1e-3) / 1e9
+    roof = {
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": achieved / peak,
+        "traffic": recorded_traffic("point_fwd_L8_grad_f32"),
+        "kernel": "point_fwd_kernel<8, GRAD, scaled, f32>",
+        "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+        "algorithmic_bytes_per_launch": bytes_per_launch,
+        "frac_of_8TBs": achieved / 8000.0,
+    }
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "points/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": f"forward values+gradients, l_max={L}, N={n} per GPU, FP32, scaled (r^l Y), "
+                "directions uniform, r~U[0.5,5]",
+                "n_points_per_gpu": n,
+                "l_max": L,
+                "outputs": f"sph [N,{K}] + dsph [N,3,{K}] FP32",
+                "l2": "flushed between timed launches (256 MB zero fill outside the timed events)",
+                "parallelism": f"points sharded, {world} independent rank(s)",
+            },
+            "roofline": roof,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+            "wall_s_timed_region": wall,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _events_ms(torch, stream, fn, reps, flush=None):
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    return statistics.median(times)
+
+
+def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
+    import oracle
+
+    out = {}
+    # ---- end to end: pinned host xyz -> device -> compute -> pinned host outputs
+    xyz_h = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).pin_memory()
+    sph_h = torch.empty((n, K), dtype=torch.float32).pin_memory()
+    dsph_h = torch.empty((n, 3, K), dtype=torch.float32).pin_memory()
+    xyz_d = torch.empty((n, 3), device=dev)
+
+    def e2e_step():
+        xyz_d.copy_(xyz_h, non_blocking=True)
+        api.spherical_harmonics(xyz_d, L, False, gradients=True, out=(sph, dsph))
+        sph_h.copy_(sph, non_blocking=True)
+        dsph_h.copy_(dsph, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / reps
+    out["e2e"] = {
+        "value": n / e2e_s,
+        "unit": "points/s",
+        "h2d_bytes_per_step": n * 12,
+        "d2h_bytes_per_step": n * K * 16,
+        "ms_per_step": e2e_s * 1e3,
+    }
+    del sph_h, dsph_h, xyz_h
+
+    # ---- fused recompute-backward vs materialise-then-contract (l_max = 6)
+    Lb = BWD_L
+    Kb = (Lb + 1) ** 2
+    xb_np = inputs.shell_points(BWD_N, 0.7, 6.0, seed=3)
+    gb_np = inputs.upstream(BWD_N, Kb, seed=33)
+    vb_np = inputs.upstream(BWD_N, 3, seed=34)
+    xb = torch.from_numpy(xb_np).to(dev)
+    gb = torch.from_numpy(gb_np).to(dev)
+    vb = torch.from_numpy(vb_np).to(dev)
+    sb = torch.empty((BWD_N, Kb), device=dev)
+    db = torch.empty((BWD_N, 3, Kb), device=dev)
+    dx = torch.empty_like(xb)
+
+    def fused():
+        api.spherical_harmonics(xb, Lb, False, out=(sb,))
+        api.backward(xb, gb, Lb, out=dx)
+
+    def plain():
+        api.spherical_harmonics(xb, Lb, False, gradients=True, out=(sb, db))
+        return torch.einsum("nik,nk->ni", db, gb)
+
+    def fused_bwd_only():
+        api.backward(xb, gb, Lb, out=dx)
+
+    for _ in range(3):
+        fused()
+        plain()
+    t_fused = _events_ms(torch, stream, fused, 10, flush)
+    t_plain = _events_ms(torch, stream, plain, 10, flush)
+    t_bwd = _events_ms(torch, stream, fused_bwd_only, 10, flush)
+    t_dbwd = _events_ms(torch, stream, lambda: api.double_backward(xb, gb, vb, Lb), 10, flush)
+    fused()
+    dx_plain = plain()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = rng.choice(BWD_N, 4096, replace=False)
+    ref = oracle.backward(xb_np[idx].astype(np.float64), gb_np[idx].astype(np.float64), Lb)
+    scale = np.max(np.abs(ref))
+    err_f = float(np.max(np.abs(dx.double().cpu().numpy()[idx] - ref)) / scale)
+    err_p = float(np.max(np.abs(dx_plain.double().cpu().numpy()[idx] - ref)) / scale)
+    # central differences in FP64 with h = 1e-3 on a few points, for context
+    sub = idx[:64]
+    xs = xb_np[sub].astype(np.float64)
+    gs = gb_np[sub].astype(np.float64)
+    fd = np.zeros_like(xs)
+    for j in range(3):
+        e = np.zeros_like(xs)
+        e[:, j] = 1e-3
+        fp = np.sum(oracle.spherical_harmonics(xs + e, Lb) * gs, axis=1)
+        fm = np.sum(oracle.spherical_harmonics(xs - e, Lb) * gs, axis=1)
+        fd[:, j] = (fp - fm) / 2e-3
+    err_fd = float(np.max(np.abs(dx.double().cpu().numpy()[sub] - fd)) / np.max(np.abs(fd)))
+    bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
+    out["backward"] = {
+        "workload": f"N={BWD_N}, l_max={Lb}, |r|~U[0.7,6], g~N(0,1), FP32",
+        "fused_fwd_plus_bwd_ms": t_fused,
+        "plain_fwd_dsph_plus_einsum_ms": t_plain,
+        "speedup_fused_vs_plain": t_plain / t_fused,
+        "fused_bwd_kernel_ms": t_bwd,
+        "fused_bwd_achieved_GBs": bwd_bytes / (t_bwd * 1e-3) / 1e9,
+        "double_backward_ms": t_dbwd,
+        "max_rel_err_vs_oracle_fused": err_f,
+        "max_rel_err_vs_oracle_plain": err_p,
+        "max_rel_err_vs_fd_h1e-3_fused": err_fd,
+    }
+    return out
+
+
+if __name__ == "__main__":
+    main()

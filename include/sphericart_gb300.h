@@ -1,0 +1,232 @@
+/*
+ * sphericart_gb300.h -- C-ABI of the GB300 (sm_103a) spherical-harmonics library.
+ *
+ * The library evaluates the real spherical harmonics of arXiv 2302.08381
+ * ("Fast evaluation of spherical harmonics with sphericart"), Section 2: for
+ * every 0 <= l <= l_max and -l <= m <= l, at n independent Cartesian points,
+ *
+ *   scaled (solid) form   Ytilde_l^m(x,y,z) = r^l Y_l^m
+ *                         = F_l^|m| Q_l^|m|(z, r) * { s_|m|, 1/sqrt2, c_m }     (Eq. real-sh-cartesian)
+ *   normalized form       Y_l^m = Ytilde_l^m(x/r, y/r, z/r)                     (Section 3)
+ *
+ * with c_m, s_m from the complex-multiplication recursion (Eq. iter-sc), Q_l^m
+ * from the recursion in z and r^2 (Eq. iter-q), prefactors F_l^m tabulated on
+ * the host in FP64 (Eq. Flm, iterative form of Appendix C), and Cartesian
+ * derivatives from Eq. iter-deri (Hessians by applying Eq. iter-deri twice).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.   xyz     [n, 3]            row-major (x, y, z per point)
+ *           sph     [n, K]            K = (l_max+1)^2, column l*l + l + m
+ *           dsph    [n, 3, K]         d/dx, d/dy, d/dz planes per point
+ *           ddsph   [n, 3, 3, K]      d^2/(dx_i dx_j), i-major
+ *           g       [n, K]            upstream gradient of sph (backward)
+ *           dxyz    [n, 3]
+ * Memory.   Every data pointer is DEVICE memory owned by the caller, unless the
+ *           entry point says "host". The library owns only its cached tables
+ *           (host FP64 tables and per-device copies), created on first use and
+ *           kept until the process exits.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *           stream). Work is enqueued asynchronously; nothing synchronises
+ *           unless stated.
+ * Errors.   Every call returns an sph_status. Argument errors are detected on
+ *           the host before any launch and return SPH_EINVAL / SPH_EUNSUPPORTED
+ *           without touching device memory. A failed launch returns SPH_ECUDA.
+ *           sphericart_last_error() gives a message for the calling thread.
+ *           The library never aborts, traps or prints.
+ * Edge.     n == 0 is a no-op returning SPH_OK. A NULL derivative output skips
+ *           that output; ddsph requires dsph.
+ * Alignment Buffers aligned to 16 bytes take the bulk-copy (TMA) path; any other
+ *           alignment of the element type takes a plain-store path. Never an error.
+ * r = 0.    Scaled outputs are the polynomials' values and derivatives at 0.
+ *           Normalized outputs at r = 0: Y_0^0 = 1/sqrt(4 pi), everything else 0.
+ */
+#ifndef SPHERICART_GB300_H
+#define SPHERICART_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every entry point. */
+typedef enum {
+    SPH_OK = 0,
+    SPH_EINVAL = 1,        /* bad argument (n < 0, l_max out of range, NULL required pointer) */
+    SPH_EUNSUPPORTED = 2,  /* valid request the library does not implement      */
+    SPH_ECUDA = 3,         /* a CUDA runtime call or launch failed               */
+    SPH_ENOMEM = 4,        /* a library-owned table could not be allocated       */
+    SPH_ETIMEOUT = 5       /* a device-side bounded wait gave up (see device_status) */
+} sph_status;
+
+/* Input / compute precision. SPH_F32: xyz, outputs and arithmetic in FP32.
+ * SPH_F64: all in FP64. */
+typedef enum { SPH_F32 = 0, SPH_F64 = 1 } sph_dtype;
+
+/* Storage type of sph/dsph/ddsph. SPH_OUT_BF16 (only with SPH_F32): values are
+ * computed in FP32 and stored as bfloat16, round-to-nearest-even (uint16 bits). */
+typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
+
+/* Precision of the Q_l^m recursion (Eq. iter-q). SPH_Q_F64 with SPH_F32 runs the
+ * Q recursion in FP64 and everything else in FP32 ("mixed"). */
+typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
+
+/* Kernel family. AUTO picks POINT when l_max <= SPH_MAX_L_POINT and no Hessian
+ * is requested, else SLICE.
+ *   POINT: one thread per point, the whole (l, m) recursion unrolled in
+ *          registers for a compile-time l_max, outputs staged in shared memory
+ *          and written with bulk (TMA) copies.
+ *   SLICE: a group of lanes per point, each lane owning the m channels
+ *          m = j, j+G, ...; any l_max <= SPH_MAX_L; direct coalesced stores. */
+typedef enum { SPH_KERNEL_AUTO = 0, SPH_KERNEL_POINT = 1, SPH_KERNEL_SLICE = 2 } sph_kernel;
+
+#define SPH_MAX_L 128
+#define SPH_MAX_L_POINT 16
+
+/* Launch shape of the POINT kernels (all zero = library default / tuned).
+ *   points_per_tile  points a warp computes per tile, 4..32, multiple of 4
+ *   warps_per_block  independent warps per CTA, 1..8
+ *   blocks_per_sm    resident CTAs per SM to size the persistent grid (0 = max)
+ *   lanes_per_point  SLICE kernels only: 8, 16 or 32 (0 = by l_max)          */
+typedef struct {
+    int32_t points_per_tile;
+    int32_t warps_per_block;
+    int32_t blocks_per_sm;
+    int32_t lanes_per_point;
+} sph_launch;
+
+/* ------------------------------------------------------------------ forward
+ * sphericart_compute: FP32 forward, the paper's problem statement (Section 3:
+ * all (l, m) up to l_max for many points, optionally derivatives).
+ *   xyz    [n,3] f32 (device)          sph   [n,K] f32 (device, required)
+ *   dsph   [n,3,K] f32 or NULL         ddsph [n,3,3,K] f32 or NULL (needs dsph)
+ *   normalized  0 = scaled r^l Y_l^m, 1 = Y_l^m on the unit sphere
+ * Returns SPH_OK, or SPH_EINVAL for n < 0, l_max outside [0, SPH_MAX_L],
+ * NULL xyz/sph, or ddsph without dsph. */
+int sphericart_compute(const float* xyz, int64_t n, int l_max, int normalized,
+                       float* sph, float* dsph, float* ddsph, void* stream);
+
+/* sphericart_compute_ex: forward with every option (same layout as above).
+ *   dtype  sph_dtype of xyz and of the arithmetic
+ *   out    sph_out storage of sph/dsph/ddsph (element size 4, 8 or 2 bytes)
+ *   qprec  sph_qprec of the Q recursion (SPH_Q_F64 with SPH_F32 only)
+ *   kernel sph_kernel family; POINT with l_max > SPH_MAX_L_POINT or with
+ *          ddsph returns SPH_EUNSUPPORTED
+ *   launch NULL or a launch shape (zeros = default)
+ * SPH_EUNSUPPORTED also for BF16 output with FP64 arithmetic. */
+int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
+                          int dtype, int out, int qprec, int kernel,
+                          const sph_launch* launch,
+                          void* sph, void* dsph, void* ddsph, void* stream);
+
+/* ----------------------------------------------------------------- backward
+ * sphericart_backward: fused recompute-backward (adjoint of the forward values).
+ *   dxyz[n, i] = sum_k g[n, k] * d sph[n, k] / d x_i
+ * recomputing the recursions of Eqs. iter-sc, iter-q and iter-deri in
+ * registers; no [n,3,K] tensor is written. The paper's PyTorch layer instead
+ * contracts the dsph materialised by the forward pass (Section 3); that path
+ * is sphericart_compute + a contraction.
+ *   xyz [n,3], g [n,K], dxyz [n,3], all of `dtype` (device).
+ * Errors as sphericart_compute_ex (kernel: AUTO, POINT or SLICE). */
+int sphericart_backward(const void* xyz, const void* g, int64_t n, int l_max,
+                        int normalized, int dtype, int kernel,
+                        const sph_launch* launch, void* dxyz, void* stream);
+
+/* sphericart_double_backward: adjoint of sphericart_backward for a cotangent
+ * v [n,3] of dxyz (forces training):
+ *   grad_g[n, k]   = sum_j v[n, j] d sph[n, k] / d x_j
+ *   grad_xyz[n, i] = sum_k g[n, k] sum_j v[n, j] d^2 sph[n, k] / d x_i d x_j
+ * Hessians come from Eq. iter-deri applied twice, in registers.
+ * Either output may be NULL (skipped). All device, all of `dtype`. */
+int sphericart_double_backward(const void* xyz, const void* g, const void* v,
+                               int64_t n, int l_max, int normalized, int dtype,
+                               int kernel, const sph_launch* launch,
+                               void* grad_g, void* grad_xyz, void* stream);
+
+/* ------------------------------------------------------------------ batched
+ * One set of a ragged batch: points xyz[n,3] f32 with their own l_max, outputs
+ * sph[n,(l_max+1)^2] and dsph[n,3,(l_max+1)^2] (dsph may be NULL). Device
+ * pointers; the descriptor array itself lives in HOST memory. */
+typedef struct {
+    const float* xyz;
+    float* sph;
+    float* dsph;
+    int64_t n;
+    int32_t l_max;
+    int32_t normalized;
+} sph_batch_set;
+
+/* Opaque plan for a ragged batch (FP32, POINT kernels, l_max <= SPH_MAX_L_POINT). */
+typedef struct sph_batch_plan sph_batch_plan;
+
+/* sphericart_batch_plan_create: builds the device work list for `nsets` sets
+ * (copied from host memory) for ONE persistent launch in which every warp pulls
+ * tiles from a device counter and branches on the set's l_max. The plan owns
+ * its device work list (allocated here, freed by _destroy). Buffers of the sets
+ * must stay valid while the plan is executed. `launch` may be NULL (default
+ * shape); points_per_tile is chosen per l_max to fit a fixed shared-memory
+ * budget per warp. Errors: SPH_EINVAL for a NULL pointer, nsets <= 0, a set
+ * with n < 0 or l_max outside [0, SPH_MAX_L_POINT]; SPH_ENOMEM / SPH_ECUDA. */
+int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets,
+                                 const sph_launch* launch, sph_batch_plan** plan);
+
+/* sphericart_batch_execute: enqueues the persistent launch (counter reset +
+ * kernel) on `stream`. Capturable in a CUDA graph. */
+int sphericart_batch_execute(const sph_batch_plan* plan, void* stream);
+
+/* sphericart_batch_plan_destroy: frees the plan (synchronises its device). */
+int sphericart_batch_plan_destroy(sph_batch_plan* plan);
+
+/* sphericart_batch_plan_info: total points and work tiles of a plan (host). */
+int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points,
+                               int64_t* total_tiles);
+
+/* ----------------------------------------------------------------- services
+ * sphericart_last_error: message of the last failed call on this thread
+ * (static storage owned by the library; valid until the next call). */
+const char* sphericart_last_error(void);
+
+/* sphericart_max_l: largest l_max a (dtype, qprec, kernel) combination takes. */
+int sphericart_max_l(int dtype, int qprec, int kernel);
+
+/* sphericart_host_table: copies the host FP64 table `which` for 0..l_max into
+ * `out` (HOST memory, (l_max+1)(l_max+2)/2 doubles, entry (l,m) at
+ * l(l+1)/2 + m). Host-only; needs no GPU.
+ *   which 0: F_l^m, Eq. Flm by the Appendix C iteration
+ *         1: Qtilde_l^l = F_l^l Q_l^l on the diagonal (0 elsewhere), Eq. iter-q
+ *         2: a_l^m, 3: b_l^m  coefficients of the folded recursion
+ *            Qtilde_l^m = a z Qtilde_{l-1}^m - b r^2 Qtilde_{l-2}^m (Eq. iter-q, App. C)
+ *         4: e_l^m = F_l^m / F_{l-1}^{m+1}       (d/dx, d/dy of Eq. iter-deri)
+ *         5: f_l^m = (l+m) F_l^m / F_{l-1}^m     (d/dz of Eq. iter-deri)
+ *         6: d_l   = (2l-1) F_l^{l-1}/F_{l-1}^{l-1} on entry (l, l-1)
+ * Tables 4 and 5 carry the 1/sqrt2 of the m = 0 column folded in.
+ * Returns SPH_EINVAL for a bad `which`, l_max or NULL out. */
+int sphericart_host_table(int l_max, int which, double* out);
+
+/* sphericart_device_status: reads and clears the device-side status word of
+ * the current device (nonzero = a bounded wait timed out inside a kernel).
+ * Synchronises the device. Returns SPH_OK and writes the word to *status. */
+int sphericart_device_status(uint32_t* status);
+
+/* sphericart_launch_info: the launch shape the library would use for a
+ * forward call (after tuning), for inspection. kernel_out receives the
+ * family (POINT or SLICE). Host-only except for a device-properties query. */
+int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess,
+                           int* kernel_out, sph_launch* launch_out);
+
+/* sphericart_set_launch: installs a tuned launch shape for forward calls with
+ * this (l_max, dtype, out, grad) on the current device; used by AUTO/POINT
+ * calls that pass launch == NULL. points_per_tile etc. are validated. */
+int sphericart_set_launch(int l_max, int dtype, int out, int grad,
+                          const sph_launch* launch);
+
+/* sphericart_version: library version as 10000*major + 100*minor + patch. */
+int sphericart_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHERICART_GB300_H */

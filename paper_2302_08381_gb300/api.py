@@ -1,0 +1,171 @@
+"""Tensor-level calls of the C-ABI: allocate outputs with torch on the input's
+device, pass raw pointers and torch's current stream, raise on any error.
+Every computation runs in the CUDA library; CPU tensors are rejected.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import _capi as C
+
+_KERNELS = {"auto": C.SPH_KERNEL_AUTO, "point": C.SPH_KERNEL_POINT, "slice": C.SPH_KERNEL_SLICE}
+_QPREC = {"native": C.SPH_Q_NATIVE, "f64": C.SPH_Q_F64}
+
+
+def n_columns(l_max: int) -> int:
+    return (l_max + 1) ** 2
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return C.SPH_F32
+    if t.dtype == torch.float64:
+        return C.SPH_F64
+    raise TypeError(f"xyz must be float32 or float64, got {t.dtype}")
+
+
+def _check_points(xyz: torch.Tensor, name: str = "xyz") -> None:
+    if not isinstance(xyz, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not xyz.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if xyz.dim() != 2 or xyz.shape[1] != 3:
+        raise ValueError(f"{name} must have shape [n, 3], got {tuple(xyz.shape)}")
+    if not xyz.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _launch(launch):
+    if launch is None:
+        return None
+    if isinstance(launch, C.sph_launch):
+        return launch
+    return C.make_launch(**launch)
+
+
+def spherical_harmonics(
+    xyz: torch.Tensor,
+    l_max: int,
+    normalized: bool = False,
+    gradients: bool = False,
+    hessians: bool = False,
+    out_dtype: torch.dtype | None = None,
+    qprec: str = "native",
+    kernel: str = "auto",
+    launch=None,
+    out=None,
+):
+    """Real spherical harmonics of every (l, m), l <= l_max, at each point.
+
+    Returns ``sph`` [n, K]; with ``gradients`` also ``dsph`` [n, 3, K]; with
+    ``hessians`` also ``ddsph`` [n, 3, 3, K]. ``normalized=False`` gives the
+    scaled r^l Y_l^m. ``out_dtype=torch.bfloat16`` stores FP32 results as
+    bfloat16 (round to nearest even). ``qprec="f64"`` runs the Q recursion in
+    FP64 with FP32 everything else. ``out`` may supply preallocated outputs.
+    """
+    _check_points(xyz)
+    dt = _dtype_code(xyz)
+    hessians = bool(hessians)
+    gradients = bool(gradients) or hessians
+    if out_dtype is None or out_dtype == xyz.dtype:
+        oc, odt = C.SPH_OUT_SAME, xyz.dtype
+    elif out_dtype == torch.bfloat16:
+        oc, odt = C.SPH_OUT_BF16, torch.bfloat16
+    else:
+        raise TypeError(f"unsupported out_dtype {out_dtype}")
+    n = xyz.shape[0]
+    K = n_columns(l_max)
+    if out is not None:
+        sph, dsph, ddsph = (list(out) + [None, None, None])[:3]
+    else:
+        sph = torch.empty((n, K), dtype=odt, device=xyz.device)
+        dsph = torch.empty((n, 3, K), dtype=odt, device=xyz.device) if gradients else None
+        ddsph = torch.empty((n, 3, 3, K), dtype=odt, device=xyz.device) if hessians else None
+    L = _launch(launch)
+    C.sphericart_compute_ex(
+        xyz.data_ptr(),
+        n,
+        l_max,
+        1 if normalized else 0,
+        dt,
+        oc,
+        _QPREC[qprec],
+        _KERNELS[kernel],
+        L,
+        sph.data_ptr() if sph is not None else None,
+        dsph.data_ptr() if dsph is not None else None,
+        ddsph.data_ptr() if ddsph is not None else None,
+        _stream(xyz.device),
+    )
+    if hessians:
+        return sph, dsph, ddsph
+    if gradients:
+        return sph, dsph
+    return sph
+
+
+def backward(xyz, g, l_max, normalized=False, kernel="auto", launch=None, out=None):
+    """Fused recompute-backward: dxyz[n, i] = sum_k g[n, k] d sph[n, k] / d x_i."""
+    _check_points(xyz)
+    g = g.contiguous()
+    if g.shape != (xyz.shape[0], n_columns(l_max)) or g.dtype != xyz.dtype or g.device != xyz.device:
+        raise ValueError("g must be [n, (l_max+1)^2] with the dtype and device of xyz")
+    dxyz = torch.empty_like(xyz) if out is None else out
+    C.sphericart_backward(
+        xyz.data_ptr(),
+        g.data_ptr(),
+        xyz.shape[0],
+        l_max,
+        1 if normalized else 0,
+        _dtype_code(xyz),
+        _KERNELS[kernel],
+        _launch(launch),
+        dxyz.data_ptr(),
+        _stream(xyz.device),
+    )
+    return dxyz
+
+
+def double_backward(xyz, g, v, l_max, normalized=False, kernel="auto", launch=None, need_g=True, need_xyz=True):
+    """grad_g[n, k] = sum_j v_j d sph_k/dx_j; grad_xyz[n, i] = sum_k g_k sum_j v_j d2 sph_k/dx_i dx_j."""
+    _check_points(xyz)
+    g = g.contiguous()
+    v = v.contiguous()
+    if g.shape != (xyz.shape[0], n_columns(l_max)) or v.shape != xyz.shape:
+        raise ValueError("g must be [n, K] and v [n, 3]")
+    grad_g = torch.empty_like(g) if need_g else None
+    grad_xyz = torch.empty_like(xyz) if need_xyz else None
+    C.sphericart_double_backward(
+        xyz.data_ptr(),
+        g.data_ptr(),
+        v.data_ptr(),
+        xyz.shape[0],
+        l_max,
+        1 if normalized else 0,
+        _dtype_code(xyz),
+        _KERNELS[kernel],
+        _launch(launch),
+        grad_g.data_ptr() if grad_g is not None else None,
+        grad_xyz.data_ptr() if grad_xyz is not None else None,
+        _stream(xyz.device),
+    )
+    return grad_g, grad_xyz
+
+
+def materialized_backward(xyz, g, l_max, normalized=False, dsph=None):
+    """The paper's PyTorch-layer backward (Section 3): the forward writes dsph,
+    then dxyz = einsum('nik,nk->ni', dsph, g). Kept as the comparator of the
+    fused backward; the einsum is torch's."""
+    if dsph is None:
+        _, dsph = spherical_harmonics(xyz, l_max, normalized, gradients=True)
+    return torch.einsum("nik,nk->ni", dsph, g)
+
+
+def device_status() -> int:
+    """Reads and clears the device status word (nonzero: a bounded wait timed out)."""
+    return C.sphericart_device_status()

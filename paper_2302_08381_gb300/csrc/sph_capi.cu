@@ -1,0 +1,474 @@
+// C-ABI entry points of libsphericart_gb300 (declared in
+// include/sphericart_gb300.h): argument validation, kernel-family dispatch,
+// launch-shape resolution, and the library-owned caches (device tables,
+// device status word, tuned launch shapes).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "sph_internal.h"
+
+namespace sph {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* last_error_message() { return g_err; }
+
+// --------------------------------------------------------- device caches
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int g_sms[kMaxDevices] = {0};
+int g_smem[kMaxDevices] = {0};
+void* g_tab32[kMaxDevices] = {nullptr};
+void* g_tab64[kMaxDevices] = {nullptr};
+uint32_t* g_status[kMaxDevices] = {nullptr};
+
+int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return (d >= 0 && d < kMaxDevices) ? d : -1;
+}
+}  // namespace
+
+int sm_count() {
+    const int d = current_device();
+    if (d < 0) return 1;
+    if (g_sms[d] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        g_sms[d] = std::max(v, 1);
+    }
+    return g_sms[d];
+}
+
+int max_smem_optin() {
+    const int d = current_device();
+    if (d < 0) return 48 * 1024;
+    if (g_smem[d] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+        g_smem[d] = std::max(v, 48 * 1024);
+    }
+    return g_smem[d];
+}
+
+const void* device_tables(int dtype) {
+    const int d = current_device();
+    if (d < 0) {
+        set_error("no current CUDA device");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    void*& slot = (dtype == SPH_F64) ? g_tab64[d] : g_tab32[d];
+    if (slot) return slot;
+    const HostTables& h = host_tables();
+    const int tn = tri_size(SPH_MAX_L);
+    const std::vector<double>* src[kSliceTables] = {&h.qll, &h.d, &h.a, &h.b, &h.e, &h.fz, &h.g2, &h.g3, &h.g4};
+    const size_t elem = (dtype == SPH_F64) ? 8 : 4;
+    std::vector<unsigned char> host(size_t(kSliceTables) * tn * elem);
+    for (int t = 0; t < kSliceTables; ++t)
+        for (int i = 0; i < tn; ++i) {
+            const double v = (*src[t])[i];
+            if (dtype == SPH_F64)
+                reinterpret_cast<double*>(host.data())[size_t(t) * tn + i] = v;
+            else
+                reinterpret_cast<float*>(host.data())[size_t(t) * tn + i] = static_cast<float>(v);
+        }
+    void* p = nullptr;
+    if (cudaMalloc(&p, host.size()) != cudaSuccess) {
+        set_error("cudaMalloc of %zu bytes for device tables failed", host.size());
+        return nullptr;
+    }
+    if (cudaMemcpy(p, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(p);
+        set_error("upload of device tables failed");
+        return nullptr;
+    }
+    slot = p;
+    return slot;
+}
+
+uint32_t* device_status_word() {
+    const int d = current_device();
+    if (d < 0) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status[d]) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(uint32_t));
+        cudaDeviceSynchronize();
+        g_status[d] = static_cast<uint32_t*>(p);
+    }
+    return g_status[d];
+}
+
+// ------------------------------------------------------------ launch shape
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int>;  // device, L, dtype, out, grad
+std::map<TuneKey, sph_launch> g_tuned;
+
+int elem_size(int dtype, int out) {
+    if (dtype == SPH_F64) return 8;
+    return out == SPH_OUT_BF16 ? 2 : 4;
+}
+
+int gcd_int(int a, int b) {
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Points per tile must keep every tile's first byte 16-byte aligned.
+int tile_multiple(int L, int elem) {
+    const int K = (L + 1) * (L + 1);
+    return 16 / gcd_int((K * elem) % 16 == 0 ? 16 : (K * elem) % 16, 16);
+}
+
+sph_launch default_point_fwd(int L, int grad, int elem) {
+    const size_t row = point_row_bytes(L, grad, elem);
+    const int mult = tile_multiple(L, elem);
+    const size_t budget = 48 * 1024;
+    int P = 32;
+    while (P > mult && size_t(P) * row > budget) P -= mult;
+    P = std::max(mult, P / mult * mult);
+    const size_t tile = size_t(P) * row;
+    int W = int(std::max<size_t>(1, std::min<size_t>(4, budget / std::max<size_t>(tile, 1))));
+    return sph_launch{P, W, 0, 0};
+}
+
+sph_launch default_point_bwd(int L, int elem, int dbw) {
+    const size_t K = size_t(L + 1) * (L + 1);
+    const int mult = tile_multiple(L, elem);
+    const size_t per_pt = K * elem * (dbw ? 3 : 2);
+    const size_t budget = 48 * 1024;
+    int P = 32;
+    while (P > mult && size_t(P) * per_pt > budget) P -= mult;
+    P = std::max(mult, P / mult * mult);
+    const size_t tile = size_t(P) * per_pt;
+    int W = int(std::max<size_t>(1, std::min<size_t>(4, budget / std::max<size_t>(tile, 1))));
+    return sph_launch{P, W, 0, 0};
+}
+
+// Validates / completes a POINT launch shape; returns false with a message.
+bool resolve_point(sph_launch& s, const sph_launch& dflt, int L, int elem, size_t per_point_bytes) {
+    if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;
+    if (s.warps_per_block == 0) s.warps_per_block = dflt.warps_per_block;
+    const int mult = tile_multiple(L, elem);
+    if (s.points_per_tile < 1 || s.points_per_tile > 32 || s.points_per_tile % mult != 0) {
+        set_error("points_per_tile=%d must be in [1,32] and a multiple of %d for l_max=%d", s.points_per_tile,
+                  mult, L);
+        return false;
+    }
+    if (s.warps_per_block < 1 || s.warps_per_block > 8) {
+        set_error("warps_per_block=%d must be in [1,8]", s.warps_per_block);
+        return false;
+    }
+    if (s.blocks_per_sm < 0 || s.blocks_per_sm > 32) {
+        set_error("blocks_per_sm=%d must be in [0,32]", s.blocks_per_sm);
+        return false;
+    }
+    const size_t smem = size_t(s.warps_per_block) * (size_t(s.points_per_tile) * per_point_bytes + 64);
+    if (smem > size_t(max_smem_optin())) {
+        set_error("launch shape needs %zu bytes of shared memory per block (limit %d)", smem, max_smem_optin());
+        return false;
+    }
+    return true;
+}
+
+bool valid_lanes(const sph_launch& s) {
+    if (s.lanes_per_point != 0 && s.lanes_per_point != 8 && s.lanes_per_point != 16 && s.lanes_per_point != 32) {
+        set_error("lanes_per_point=%d must be 0, 8, 16 or 32", s.lanes_per_point);
+        return false;
+    }
+    if (s.blocks_per_sm < 0 || s.blocks_per_sm > 32) {
+        set_error("blocks_per_sm=%d must be in [0,32]", s.blocks_per_sm);
+        return false;
+    }
+    return true;
+}
+
+bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+
+int cuda_status(int err, const char* what) {
+    if (err == 0) return SPH_OK;
+    set_error("%s: %s", what, cudaGetErrorString(static_cast<cudaError_t>(err)));
+    return SPH_ECUDA;
+}
+
+// Common checks; returns SPH_OK or an error (message set).
+int check_common(int64_t n, int l_max, int dtype, int kernel) {
+    if (n < 0) {
+        set_error("n=%lld must be >= 0", static_cast<long long>(n));
+        return SPH_EINVAL;
+    }
+    if (l_max < 0 || l_max > SPH_MAX_L) {
+        set_error("l_max=%d must be in [0,%d]", l_max, SPH_MAX_L);
+        return SPH_EINVAL;
+    }
+    if (dtype != SPH_F32 && dtype != SPH_F64) {
+        set_error("dtype=%d is not an sph_dtype", dtype);
+        return SPH_EINVAL;
+    }
+    if (kernel != SPH_KERNEL_AUTO && kernel != SPH_KERNEL_POINT && kernel != SPH_KERNEL_SLICE) {
+        set_error("kernel=%d is not an sph_kernel", kernel);
+        return SPH_EINVAL;
+    }
+    return SPH_OK;
+}
+
+int ensure_device(const char* what) {
+    int d = -1;
+    const cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) {
+        set_error("%s: no usable CUDA device (%s)", what, cudaGetErrorString(e));
+        cudaGetLastError();
+        return SPH_ECUDA;
+    }
+    return SPH_OK;
+}
+
+}  // namespace
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+int sphericart_version(void) { return 10000; }
+
+const char* sphericart_last_error(void) { return last_error_message(); }
+
+int sphericart_max_l(int dtype, int qprec, int kernel) {
+    if (kernel == SPH_KERNEL_POINT) return (qprec == SPH_Q_F64 && dtype == SPH_F32) ? -1 : SPH_MAX_L_POINT;
+    (void)dtype;
+    return SPH_MAX_L;
+}
+
+int sphericart_host_table(int l_max, int which, double* out) {
+    if (!out || l_max < 0 || l_max > SPH_MAX_L || which < 0 || which > 6) {
+        set_error("host_table: bad arguments (l_max=%d which=%d)", l_max, which);
+        return SPH_EINVAL;
+    }
+    const HostTables& h = host_tables();
+    const std::vector<double>* src[] = {&h.F, &h.qll, &h.a, &h.b, &h.e, &h.fz, &h.d};
+    std::memcpy(out, src[which]->data(), sizeof(double) * size_t(tri_size(l_max)));
+    return SPH_OK;
+}
+
+int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized, int dtype, int out, int qprec,
+                          int kernel, const sph_launch* launch, void* sph, void* dsph, void* ddsph,
+                          void* stream) {
+    int st = check_common(n, l_max, dtype, kernel);
+    if (st) return st;
+    if (out != SPH_OUT_SAME && out != SPH_OUT_BF16) {
+        set_error("out=%d is not an sph_out", out);
+        return SPH_EINVAL;
+    }
+    if (qprec != SPH_Q_NATIVE && qprec != SPH_Q_F64) {
+        set_error("qprec=%d is not an sph_qprec", qprec);
+        return SPH_EINVAL;
+    }
+    if (ddsph && !dsph) {
+        set_error("ddsph requires dsph");
+        return SPH_EINVAL;
+    }
+    if (dtype == SPH_F64 && out == SPH_OUT_BF16) {
+        set_error("bfloat16 output is only available with FP32 arithmetic");
+        return SPH_EUNSUPPORTED;
+    }
+    const bool mixed = (dtype == SPH_F32 && qprec == SPH_Q_F64);
+    const int grad = dsph ? 1 : 0;
+    int fam = kernel;
+    if (fam == SPH_KERNEL_AUTO) fam = (l_max <= SPH_MAX_L_POINT && !ddsph && !mixed) ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE;
+    if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || ddsph || mixed)) {
+        set_error("POINT kernels take l_max <= %d, no Hessians and native Q precision", SPH_MAX_L_POINT);
+        return SPH_EUNSUPPORTED;
+    }
+    if (n == 0) return SPH_OK;
+    if (!xyz || !sph) {
+        set_error("xyz and sph must be non-NULL");
+        return SPH_EINVAL;
+    }
+    const int ein = dtype == SPH_F64 ? 8 : 4;
+    const int eo = elem_size(dtype, out);
+    if (!aligned(xyz, ein) || !aligned(sph, eo) || (dsph && !aligned(dsph, eo)) || (ddsph && !aligned(ddsph, eo))) {
+        set_error("buffers must be aligned to their element size");
+        return SPH_EINVAL;
+    }
+    st = ensure_device("compute");
+    if (st) return st;
+
+    FwdArgs a{xyz, n, l_max, normalized ? 1 : 0, dtype, out, qprec, sph, dsph, ddsph, stream, sph_launch{0, 0, 0, 0},
+              nullptr};
+    if (launch) a.launch = *launch;
+    if (fam == SPH_KERNEL_POINT) {
+        if (!launch) {
+            int d = -1;
+            cudaGetDevice(&d);
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, grad});
+            if (it != g_tuned.end()) a.launch = it->second;
+        }
+        const sph_launch dflt = default_point_fwd(l_max, grad, eo);
+        if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo))) return SPH_EINVAL;
+        return cuda_status(point_fwd_fn(l_max)(a), "POINT forward launch");
+    }
+    if (!valid_lanes(a.launch)) return SPH_EINVAL;
+    return cuda_status(slice_fwd(a), "SLICE forward launch");
+}
+
+int sphericart_compute(const float* xyz, int64_t n, int l_max, int normalized, float* sph, float* dsph,
+                       float* ddsph, void* stream) {
+    return sphericart_compute_ex(xyz, n, l_max, normalized, SPH_F32, SPH_OUT_SAME, SPH_Q_NATIVE, SPH_KERNEL_AUTO,
+                                 nullptr, sph, dsph, ddsph, stream);
+}
+
+static int backward_common(const void* xyz, const void* g, const void* v, int64_t n, int l_max, int normalized,
+                           int dtype, int kernel, const sph_launch* launch, void* dxyz, void* grad_g,
+                           void* grad_xyz, void* stream, bool dbw) {
+    int st = check_common(n, l_max, dtype, kernel);
+    if (st) return st;
+    int fam = kernel == SPH_KERNEL_AUTO ? (l_max <= SPH_MAX_L_POINT ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE) : kernel;
+    if (fam == SPH_KERNEL_POINT && l_max > SPH_MAX_L_POINT) {
+        set_error("POINT kernels take l_max <= %d", SPH_MAX_L_POINT);
+        return SPH_EUNSUPPORTED;
+    }
+    if (n == 0) return SPH_OK;
+    if (!xyz || !g || (dbw && !v) || (!dbw && !dxyz)) {
+        set_error("xyz, g%s must be non-NULL", dbw ? ", v" : ", dxyz");
+        return SPH_EINVAL;
+    }
+    if (dbw && !grad_g && !grad_xyz) return SPH_OK;
+    const int e = dtype == SPH_F64 ? 8 : 4;
+    if (!aligned(xyz, e) || !aligned(g, e) || (v && !aligned(v, e)) || (dxyz && !aligned(dxyz, e)) ||
+        (grad_g && !aligned(grad_g, e)) || (grad_xyz && !aligned(grad_xyz, e))) {
+        set_error("buffers must be aligned to their element size");
+        return SPH_EINVAL;
+    }
+    st = ensure_device(dbw ? "double_backward" : "backward");
+    if (st) return st;
+    BwdArgs a{xyz, g, v, n, l_max, normalized ? 1 : 0, dtype, dxyz, grad_g, grad_xyz, stream,
+              sph_launch{0, 0, 0, 0}, nullptr};
+    if (launch) a.launch = *launch;
+    if (fam == SPH_KERNEL_POINT) {
+        a.status = device_status_word();
+        if (!a.status) {
+            set_error("could not allocate the device status word");
+            return SPH_ENOMEM;
+        }
+        const size_t K = size_t(l_max + 1) * (l_max + 1);
+        if (!resolve_point(a.launch, default_point_bwd(l_max, e, dbw), l_max, e, K * e * (dbw ? 3 : 2)))
+            return SPH_EINVAL;
+        PointBwdFn fn = dbw ? point_dbwd_fn(l_max) : point_bwd_fn(l_max);
+        return cuda_status(fn(a), dbw ? "POINT double-backward launch" : "POINT backward launch");
+    }
+    if (!valid_lanes(a.launch)) return SPH_EINVAL;
+    return cuda_status(dbw ? slice_dbwd(a) : slice_bwd(a), dbw ? "SLICE double-backward launch" : "SLICE backward launch");
+}
+
+int sphericart_backward(const void* xyz, const void* g, int64_t n, int l_max, int normalized, int dtype, int kernel,
+                        const sph_launch* launch, void* dxyz, void* stream) {
+    return backward_common(xyz, g, nullptr, n, l_max, normalized, dtype, kernel, launch, dxyz, nullptr, nullptr,
+                           stream, false);
+}
+
+int sphericart_double_backward(const void* xyz, const void* g, const void* v, int64_t n, int l_max, int normalized,
+                               int dtype, int kernel, const sph_launch* launch, void* grad_g, void* grad_xyz,
+                               void* stream) {
+    return backward_common(xyz, g, v, n, l_max, normalized, dtype, kernel, launch, nullptr, grad_g, grad_xyz, stream,
+                           true);
+}
+
+int sphericart_device_status(uint32_t* status) {
+    if (!status) {
+        set_error("status must be non-NULL");
+        return SPH_EINVAL;
+    }
+    int st = ensure_device("device_status");
+    if (st) return st;
+    uint32_t* w = device_status_word();
+    if (!w) {
+        set_error("could not allocate the device status word");
+        return SPH_ENOMEM;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, w, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return cuda_status(int(e), "device_status");
+}
+
+int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, int* kernel_out,
+                           sph_launch* launch_out) {
+    if (!kernel_out || !launch_out || l_max < 0 || l_max > SPH_MAX_L || (dtype != SPH_F32 && dtype != SPH_F64) ||
+        (out != SPH_OUT_SAME && out != SPH_OUT_BF16)) {
+        set_error("launch_info: bad arguments");
+        return SPH_EINVAL;
+    }
+    const int eo = elem_size(dtype, out);
+    if (l_max <= SPH_MAX_L_POINT && !hess) {
+        *kernel_out = SPH_KERNEL_POINT;
+        sph_launch s{0, 0, 0, 0};
+        int d = -1;
+        if (cudaGetDevice(&d) != cudaSuccess) {
+            cudaGetLastError();
+            d = -1;
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, grad ? 1 : 0});
+            if (it != g_tuned.end()) s = it->second;
+        }
+        const sph_launch dflt = default_point_fwd(l_max, grad ? 1 : 0, eo);
+        if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;
+        if (s.warps_per_block == 0) s.warps_per_block = dflt.warps_per_block;
+        *launch_out = s;
+    } else {
+        *kernel_out = SPH_KERNEL_SLICE;
+        *launch_out = sph_launch{0, 0, 0, l_max + 1 <= 8 ? 8 : (l_max + 1 <= 16 ? 16 : 32)};
+    }
+    return SPH_OK;
+}
+
+int sphericart_set_launch(int l_max, int dtype, int out, int grad, const sph_launch* launch) {
+    if (!launch || l_max < 0 || l_max > SPH_MAX_L_POINT || (dtype != SPH_F32 && dtype != SPH_F64) ||
+        (out != SPH_OUT_SAME && out != SPH_OUT_BF16)) {
+        set_error("set_launch: bad arguments");
+        return SPH_EINVAL;
+    }
+    int st = ensure_device("set_launch");
+    if (st) return st;
+    const int eo = elem_size(dtype, out);
+    sph_launch s = *launch;
+    if (!resolve_point(s, default_point_fwd(l_max, grad ? 1 : 0, eo), l_max, eo,
+                       point_row_bytes(l_max, grad ? 1 : 0, eo)))
+        return SPH_EINVAL;
+    int d = -1;
+    cudaGetDevice(&d);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned[TuneKey{d, l_max, dtype, out, grad ? 1 : 0}] = s;
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal host-side declarations shared by the translation units of the
+// library. Not part of the public C-ABI (see include/sphericart_gb300.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "sphericart_gb300.h"
+
+#ifdef __CUDACC__
+#define SPH_HD __host__ __device__
+#else
+#define SPH_HD
+#endif
+
+namespace sph {
+
+// Triangular index of (l, m), 0 <= m <= l.
+SPH_HD inline constexpr int tri(int l, int m) { return l * (l + 1) / 2 + m; }
+SPH_HD inline constexpr int tri_size(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Host FP64 tables for 0 <= l <= SPH_MAX_L (arXiv 2302.08381, Eq. Flm via the
+// Appendix C iteration; the folded recursion coefficients of Appendix C; the
+// derivative multipliers of Eq. iter-deri). All in triangular layout.
+struct HostTables {
+    int lmax = 0;
+    std::vector<double> F;    // F_l^m
+    std::vector<double> qll;  // Qtilde_l^l on (l,l), zero elsewhere
+    std::vector<double> d;    // (2l-1) F_l^{l-1}/F_{l-1}^{l-1} on (l,l-1)
+    std::vector<double> a;    // (2l-1)/(l-m) F_l^m/F_{l-1}^m       m <= l-2
+    std::vector<double> b;    // (l+m-1)/(l-m) F_l^m/F_{l-2}^m      m <= l-2
+    std::vector<double> e;    // F_l^m/F_{l-1}^{m+1}                m <= l-2  (x 1/sqrt2 at m=0)
+    std::vector<double> fz;   // (l+m) F_l^m/F_{l-1}^m              m <= l-1  (x 1/sqrt2 at m=0)
+    std::vector<double> g2;   // F_l^m/F_{l-2}^{m+2}                m <= l-4  (x 1/sqrt2 at m=0)
+    std::vector<double> g3;   // (l+m) F_l^m/F_{l-2}^{m+1}          m <= l-3  (x 1/sqrt2 at m=0)
+    std::vector<double> g4;   // (l+m)(l+m-1) F_l^m/F_{l-2}^m       m <= l-2  (x 1/sqrt2 at m=0)
+    double inv_sqrt2 = 0.0;   // the 1/sqrt2 of the m = 0 column (Eq. real-sh-cartesian)
+};
+
+const HostTables& host_tables();
+
+// Number of per-(l,m) tables packed for the SLICE kernels, in this order:
+// qll, d, a, b, e, fz, g2, g3, g4.
+constexpr int kSliceTables = 9;
+
+// Device copy of the packed tables for the current device, FP32 or FP64.
+// Returns nullptr and sets the error message on failure.
+const void* device_tables(int dtype);
+
+// Per-device status word written by kernels whose bounded waits time out.
+uint32_t* device_status_word();
+
+// Thread-local error message.
+void set_error(const char* fmt, ...);
+const char* last_error_message();
+
+int sm_count();            // of the current device
+int max_smem_optin();      // bytes of opt-in dynamic shared memory per block
+
+// ----------------------------------------------------------------- launches
+struct FwdArgs {
+    const void* xyz;
+    int64_t n;
+    int l_max;
+    int normalized;
+    int dtype;
+    int out;
+    int qprec;
+    void* sph;
+    void* dsph;
+    void* ddsph;
+    void* stream;
+    sph_launch launch;   // resolved launch shape
+    uint32_t* status;
+};
+
+struct BwdArgs {
+    const void* xyz;
+    const void* g;
+    const void* v;
+    int64_t n;
+    int l_max;
+    int normalized;
+    int dtype;
+    void* dxyz;      // backward output
+    void* grad_g;    // double backward outputs
+    void* grad_xyz;
+    void* stream;
+    sph_launch launch;
+    uint32_t* status;
+};
+
+// POINT kernels, one translation unit per compile-time l_max.
+// Each returns a cudaError_t value as int (0 = success).
+using PointFwdFn = int (*)(const FwdArgs&);
+using PointBwdFn = int (*)(const BwdArgs&);
+PointFwdFn point_fwd_fn(int L);
+PointBwdFn point_bwd_fn(int L);
+PointBwdFn point_dbwd_fn(int L);
+
+// Bytes of one output row of the POINT forward for this request.
+size_t point_row_bytes(int L, int grad, int elem);
+
+// SLICE kernels (runtime l_max).
+int slice_fwd(const FwdArgs& a);
+int slice_bwd(const BwdArgs& a);
+int slice_dbwd(const BwdArgs& a);
+
+}  // namespace sph

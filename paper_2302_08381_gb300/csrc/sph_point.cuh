@@ -1,0 +1,500 @@
+// POINT kernel family: one thread owns one point and runs the whole recursion
+// for a compile-time l_max in registers (arXiv 2302.08381, Section 2:
+// Eq. iter-sc for c_m/s_m, Eq. iter-q for Q_l^m with the prefactor folded in
+// as in Appendix C, Eq. iter-deri for derivatives).
+//
+// Work decomposition: every warp is independent. It takes tiles of P points
+// (P <= 32, lanes >= P idle) from a persistent grid-stride loop. Outputs of a
+// tile are contiguous in global memory ([P, K] for sph, [P, 3, K] for dsph), so
+// lanes write their rows into a shared-memory image of that range and one lane
+// sends it with a bulk (TMA) copy; with K odd (even l_max) the row stride is
+// odd and the per-lane stores are bank-conflict free. Backward kernels read
+// their [P, K] upstream-gradient tile the same way, double buffered with
+// mbarrier-tracked bulk loads.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "sph_core.cuh"
+#include "sph_internal.h"
+
+namespace sph {
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Tables passed by value as kernel parameters (constant bank), so every
+// coefficient is an immediate constant-bank operand of the FMA that uses it.
+template <int L, typename T, bool HESS>
+struct PointTabs {
+    static constexpr int TRI = (L + 1) * (L + 2) / 2;
+    static constexpr int TRIH = HESS ? TRI : 1;
+    T qll[L + 1];
+    T d[L + 1];
+    T a[TRI];
+    T b[TRI];
+    T e[TRI];
+    T fz[TRI];
+    T g2[TRIH];
+    T g3[TRIH];
+    T g4[TRIH];
+    T inv_sqrt2;
+};
+
+template <int L, typename T, bool HESS>
+PointTabs<L, T, HESS> make_point_tabs() {
+    const HostTables& h = host_tables();
+    PointTabs<L, T, HESS> t;
+    std::memset(&t, 0, sizeof(t));
+    for (int l = 0; l <= L; ++l) {
+        t.qll[l] = static_cast<T>(h.qll[tri(l, l)]);
+        t.d[l] = (l >= 1) ? static_cast<T>(h.d[tri(l, l - 1)]) : T(0);
+        for (int m = 0; m <= l; ++m) {
+            const int i = tri(l, m);
+            t.a[i] = static_cast<T>(h.a[i]);
+            t.b[i] = static_cast<T>(h.b[i]);
+            t.e[i] = static_cast<T>(h.e[i]);
+            t.fz[i] = static_cast<T>(h.fz[i]);
+            if (HESS) {
+                t.g2[i] = static_cast<T>(h.g2[i]);
+                t.g3[i] = static_cast<T>(h.g3[i]);
+                t.g4[i] = static_cast<T>(h.g4[i]);
+            }
+        }
+    }
+    t.inv_sqrt2 = static_cast<T>(h.inv_sqrt2);
+    return t;
+}
+
+// The unrolled recursion for one point. (x, y, z, r2) are the coordinates the
+// polynomials are evaluated at (already divided by r for the normalized form).
+// Calls vis.emit(l, k, Deriv) once per output column k = l*l + l + m.
+template <int L, bool GRAD, bool HESS, typename T, typename Tabs, typename Vis>
+__device__ __forceinline__ void point_core(T x, T y, T z, T r2, const Tabs& tb, Vis& vis) {
+    T c[L + 1], s[L + 1];
+    c[0] = T(1);
+    s[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {  // Eq. iter-sc
+        c[m] = x * c[m - 1] - y * s[m - 1];
+        s[m] = x * s[m - 1] + y * c[m - 1];
+    }
+    T q1[L + 1], q2[L + 1];  // Qtilde_{l-1}^m, Qtilde_{l-2}^m
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        q1[m] = T(0);
+        q2[m] = T(0);
+    }
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+        T q[L + 1];
+        q[l] = tb.qll[l];
+        if (l >= 1) q[l - 1] = tb.d[l] * z * q1[l - 1];
+#pragma unroll
+        for (int m = 0; m + 2 <= l; ++m) {  // Eq. iter-q, folded
+            const int i = tri(l, m);
+            q[m] = (tb.a[i] * z) * q1[m] - (tb.b[i] * r2) * q2[m];
+        }
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            const int i = tri(l, m);
+            QParts<T> qp;
+            qp.Q = q[m];
+            qp.E1 = (m + 1 <= l - 1) ? tb.e[i] * q1[m + 1] : T(0);
+            qp.Qz = (m <= l - 1) ? tb.fz[i] * q1[m] : T(0);
+            if constexpr (HESS) {
+                qp.G2 = (m + 2 <= l - 2) ? tb.g2[i] * q2[m + 2] : T(0);
+                qp.G3 = (m + 1 <= l - 2) ? tb.g3[i] * q2[m + 1] : T(0);
+                qp.G4 = (m <= l - 2) ? tb.g4[i] * q2[m] : T(0);
+            } else {
+                qp.G2 = qp.G3 = qp.G4 = T(0);
+            }
+            if (m == 0) {
+                Deriv<T> d = assemble_m0<GRAD, HESS>(qp, x, y, tb.inv_sqrt2);
+                vis.emit(l, l * l + l, d);
+            } else {
+                Deriv<T> dc, ds;
+                const T cm2 = (m >= 2) ? c[m >= 2 ? m - 2 : 0] : T(0);
+                const T sm2 = (m >= 2) ? s[m >= 2 ? m - 2 : 0] : T(0);
+                assemble_m<GRAD, HESS>(qp, x, y, T(m), T(m - 1), c[m], s[m], c[m - 1], s[m - 1], cm2, sm2, dc,
+                                       ds);
+                vis.emit(l, l * l + l + m, dc);
+                vis.emit(l, l * l + l - m, ds);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            q2[m] = q1[m];
+            q1[m] = q[m];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ forward
+template <typename T, typename TO, bool GRAD, bool NORM, int K>
+struct FwdVis {
+    TO* rv;  // this lane's sph row in shared memory
+    TO* rd;  // this lane's dsph row (3 planes of K)
+    T ux, uy, uz, ir;
+    __device__ __forceinline__ void emit(int l, int k, Deriv<T> d) {
+        if (GRAD) {
+            if (NORM) normalize_deriv<false>(d, l, ux, uy, uz, ir);
+            rd[k] = OutConv<TO>::cv(d.gx);
+            rd[K + k] = OutConv<TO>::cv(d.gy);
+            rd[2 * K + k] = OutConv<TO>::cv(d.gz);
+        }
+        rv[k] = OutConv<TO>::cv(d.v);
+    }
+};
+
+template <int L, bool GRAD, typename TO>
+__host__ __device__ constexpr size_t point_fwd_warp_bytes(int P) {
+    return align16(size_t(P) * (L + 1) * (L + 1) * sizeof(TO)) +
+           (GRAD ? align16(size_t(P) * 3 * (L + 1) * (L + 1) * sizeof(TO)) : 0);
+}
+
+template <int L, bool GRAD, bool NORM, typename T, typename TO>
+__global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xyz, int64_t n,
+                                                        const __grid_constant__ PointTabs<L, T, false> tb,
+                                                        TO* __restrict__ sph, TO* __restrict__ dsph, int P,
+                                                        int bulk) {
+    constexpr int K = (L + 1) * (L + 1);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const size_t vbytes = align16(size_t(P) * K * sizeof(TO));
+    TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point_fwd_warp_bytes<L, GRAD, TO>(P));
+    TO* s_d = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_v) + vbytes);
+
+    const int64_t ntiles = (n + P - 1) / P;
+    const int64_t stride = int64_t(gridDim.x) * W;
+    int64_t tile = int64_t(blockIdx.x) * W + warp;
+
+    // Software-pipelined coordinate loads: the next tile's point is fetched
+    // while the current one is computed.
+    T nx = T(0), ny = T(0), nz = T(0);
+    if (tile < ntiles && lane < P) {
+        const int64_t p = tile * P + lane;
+        if (p < n) {
+            nx = xyz[3 * p];
+            ny = xyz[3 * p + 1];
+            nz = xyz[3 * p + 2];
+        }
+    }
+    for (; tile < ntiles; tile += stride) {
+        T x = nx, y = ny, z = nz;
+        const int64_t nt = tile + stride;
+        if (nt < ntiles && lane < P) {
+            const int64_t p = nt * P + lane;
+            if (p < n) {
+                nx = xyz[3 * p];
+                ny = xyz[3 * p + 1];
+                nz = xyz[3 * p + 2];
+            }
+        }
+        const int64_t p0 = tile * P;
+        const int cnt = int(min(int64_t(P), n - p0));
+        if (lane < cnt) {
+            T r2, ir = T(1);
+            if (NORM) {
+                unit_point(x, y, z, r2, ir);
+            } else {
+                r2 = x * x + y * y + z * z;
+            }
+            FwdVis<T, TO, GRAD, NORM, K> vis{s_v + size_t(lane) * K, s_d + size_t(lane) * 3 * K, x, y, z, ir};
+            point_core<L, GRAD, false>(x, y, z, r2, tb, vis);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        const int64_t ev = int64_t(cnt) * K;  // elements of the sph tile
+        int64_t ev_bulk = 0, ed_bulk = 0;
+        if (bulk) {
+            ev_bulk = (ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
+            ed_bulk = GRAD ? (3 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO)) : 0;
+            if (lane == 0) {
+                if (ev_bulk) bulk_store(sph + p0 * K, s_v, uint32_t(ev_bulk * sizeof(TO)));
+                if (GRAD && ed_bulk) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * sizeof(TO)));
+                bulk_commit();
+            }
+        }
+        // Ragged remainder (and everything, without bulk copies): plain stores.
+        for (int64_t i = ev_bulk + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
+        if (GRAD)
+            for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
+        if (bulk && lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    }
+    if (bulk && lane == 0) bulk_wait_all();
+}
+
+// ----------------------------------------------------------------- backward
+// Loads the [cnt, K] tile of `src` at element offset `off` into `dst`: the
+// 16-byte-multiple prefix by a bulk copy on `bar` (if `bulk`), the rest with
+// plain loads at consumption time. Returns the number of bulk elements.
+template <typename T>
+__device__ __forceinline__ int64_t issue_tile_load(T* dst, const T* src, int64_t elems, int bulk, uint64_t* bar,
+                                                   int lane) {
+    int64_t eb = bulk ? (elems * int64_t(sizeof(T))) / 16 * 16 / int64_t(sizeof(T)) : 0;
+    if (eb > 0 && lane == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t(eb * sizeof(T)));
+        bulk_load(dst, src, uint32_t(eb * sizeof(T)), bar);
+    }
+    return eb;
+}
+
+constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait (>> any real load latency)
+
+template <typename T, bool NORM, int K>
+struct BwdVis {
+    const T* gr;  // this lane's upstream-gradient row in shared memory
+    T ax, ay, az, S;
+    __device__ __forceinline__ void emit(int l, int k, const Deriv<T>& d) {
+        const T gk = gr[k];
+        ax += gk * d.gx;
+        ay += gk * d.gy;
+        az += gk * d.gz;
+        if (NORM) S += gk * (T(l) * d.v);
+    }
+};
+
+template <typename T, bool NORM, int K>
+struct DbwdVis {
+    const T* gr;  // upstream gradient row (shared)
+    T* orow;      // grad_g row (shared)
+    T vx, vy, vz;
+    T ux, uy, uz, ir;
+    T ax, ay, az;
+    __device__ __forceinline__ void emit(int l, int k, Deriv<T> d) {
+        if (NORM) normalize_deriv<true>(d, l, ux, uy, uz, ir);
+        const T gk = gr[k];
+        orow[k] = vx * d.gx + vy * d.gy + vz * d.gz;
+        ax += gk * (d.hxx * vx + d.hxy * vy + d.hxz * vz);
+        ay += gk * (d.hxy * vx + d.hyy * vy + d.hyz * vz);
+        az += gk * (d.hxz * vx + d.hyz * vy + d.hzz * vz);
+    }
+};
+
+template <int L, typename T>
+__host__ __device__ constexpr size_t point_bwd_buf_bytes(int P) {
+    return align16(size_t(P) * (L + 1) * (L + 1) * sizeof(T));
+}
+
+// DBW = false: backward (dxyz). DBW = true: double backward (grad_g, grad_xyz).
+// Shared memory per warp: two upstream-gradient buffers, (DBW) one grad_g
+// buffer, and two mbarriers.
+template <int L, bool NORM, bool DBW, typename T>
+__global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xyz, const T* __restrict__ g,
+                                                        const T* __restrict__ v, int64_t n,
+                                                        const __grid_constant__ PointTabs<L, T, DBW> tb,
+                                                        T* __restrict__ dxyz, T* __restrict__ grad_g,
+                                                        T* __restrict__ grad_xyz, int P, int bulk_in,
+                                                        int bulk_out, uint32_t* __restrict__ status) {
+    constexpr int K = (L + 1) * (L + 1);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const size_t buf = point_bwd_buf_bytes<L, T>(P);
+    const size_t per_warp = (DBW ? 3 : 2) * buf + 16;
+    unsigned char* base = smem + size_t(warp) * per_warp;
+    T* const sg0 = reinterpret_cast<T*>(base);
+    T* const sg1 = reinterpret_cast<T*>(base + buf);
+    T* so = reinterpret_cast<T*>(base + 2 * buf);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (DBW ? 3 : 2) * buf);
+
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+
+    const int64_t ntiles = (n + P - 1) / P;
+    const int64_t stride = int64_t(gridDim.x) * W;
+    int64_t tile = int64_t(blockIdx.x) * W + warp;
+    uint32_t phase = 0;    // bit b: parity of buffer b's next completion
+    uint32_t pending = 0;  // bit b: a bulk load into buffer b is in flight
+    int64_t eb0 = 0, eb1 = 0;
+    bool failed = false;
+
+    if (tile < ntiles) {
+        const int64_t p0 = tile * P;
+        const int64_t cnt = min(int64_t(P), n - p0);
+        eb0 = issue_tile_load(sg0, g + p0 * K, cnt * K, bulk_in, &bar[0], lane);
+        if (eb0 > 0) pending |= 1u;
+    }
+    int cur = 0;
+    for (; tile < ntiles; tile += stride) {
+        const int64_t p0 = tile * P;
+        const int cnt = int(min(int64_t(P), n - p0));
+        // Prefetch the next tile into the other buffer; its previous contents
+        // were consumed in the last iteration, which ended with a proxy fence
+        // and __syncwarp.
+        const int64_t nt = tile + stride;
+        const int nxt = cur ^ 1;
+        if (nt < ntiles) {
+            const int64_t q0 = nt * P;
+            const int64_t qc = min(int64_t(P), n - q0);
+            const int64_t e = issue_tile_load(nxt ? sg1 : sg0, g + q0 * K, qc * K, bulk_in, &bar[nxt], lane);
+            if (nxt) eb1 = e; else eb0 = e;
+            if (e > 0) pending |= (1u << nxt);
+        }
+        // Wait for this tile's bulk part, then load the remainder directly.
+        if (pending & (1u << cur)) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&bar[cur], (phase >> cur) & 1u, kWaitPolls);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (ok) {
+                phase ^= (1u << cur);
+                pending &= ~(1u << cur);
+            } else {
+                if (lane == 0) atomicOr(status, kStatusLoadTimeout);
+                failed = true;
+            }
+        }
+        if (failed) break;
+        const int64_t eb_cur = cur ? eb1 : eb0;
+        T* const gt = cur ? sg1 : sg0;
+        for (int64_t i = eb_cur + lane; i < int64_t(cnt) * K; i += 32) gt[i] = g[p0 * K + i];
+        __syncwarp();
+        if (lane < cnt) {
+            const int64_t p = p0 + lane;
+            T x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+            T r2, ir = T(1);
+            if (NORM) {
+                unit_point(x, y, z, r2, ir);
+            } else {
+                r2 = x * x + y * y + z * z;
+            }
+            if constexpr (!DBW) {
+                BwdVis<T, NORM, K> vis{gt + size_t(lane) * K, T(0), T(0), T(0), T(0)};
+                point_core<L, true, false>(x, y, z, r2, tb, vis);
+                T ax = vis.ax, ay = vis.ay, az = vis.az;
+                if (NORM) {
+                    ax = ir * (ax - x * vis.S);
+                    ay = ir * (ay - y * vis.S);
+                    az = ir * (az - z * vis.S);
+                }
+                dxyz[3 * p] = ax;
+                dxyz[3 * p + 1] = ay;
+                dxyz[3 * p + 2] = az;
+            } else {
+                DbwdVis<T, NORM, K> vis{gt + size_t(lane) * K,
+                                        so + size_t(lane) * K,
+                                        v[3 * p],
+                                        v[3 * p + 1],
+                                        v[3 * p + 2],
+                                        x,
+                                        y,
+                                        z,
+                                        ir,
+                                        T(0),
+                                        T(0),
+                                        T(0)};
+                point_core<L, true, true>(x, y, z, r2, tb, vis);
+                if (grad_xyz) {
+                    grad_xyz[3 * p] = vis.ax;
+                    grad_xyz[3 * p + 1] = vis.ay;
+                    grad_xyz[3 * p + 2] = vis.az;
+                }
+            }
+        }
+        if constexpr (DBW) {
+            if (grad_g) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                const int64_t ev = int64_t(cnt) * K;
+                int64_t eo = 0;
+                if (bulk_out) {
+                    eo = (ev * int64_t(sizeof(T))) / 16 * 16 / int64_t(sizeof(T));
+                    if (lane == 0 && eo > 0) {
+                        bulk_store(grad_g + p0 * K, so, uint32_t(eo * sizeof(T)));
+                        bulk_commit();
+                    }
+                }
+                for (int64_t i = eo + lane; i < ev; i += 32) grad_g[p0 * K + i] = so[i];
+                if (bulk_out && lane == 0) bulk_wait_read_all();
+            }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        cur = nxt;
+    }
+    if (pending && lane == 0) {
+        // Loads issued but never observed (after a timeout) may still be in
+        // flight: wait for them, bounded, before the shared memory goes away.
+        for (int b = 0; b < 2; ++b)
+            if (pending & (1u << b)) (void)mbar_wait_bounded(&bar[b], (phase >> b) & 1u, kWaitPolls);
+    }
+    if (DBW && lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- launchers
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raise the dynamic shared-memory limit of `kern` once per device and size.
+template <typename K>
+inline cudaError_t ensure_smem(K kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(bytes));
+}
+
+template <typename K>
+inline int grid_for(K kern, int threads, size_t smem, int64_t work_warps, int blocks_per_sm) {
+    int bps = blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), threads,
+                                                          smem) != cudaSuccess)
+            occ = 1;
+        bps = std::max(occ, 1);
+    }
+    const int W = threads / 32;
+    int64_t want = ceil_div(work_warps, W);
+    int64_t cap = int64_t(bps) * sm_count();
+    return int(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+template <int L, bool GRAD, bool NORM, typename T, typename TO>
+int launch_point_fwd(const FwdArgs& a) {
+    static const PointTabs<L, T, false> tb = make_point_tabs<L, T, false>();
+    const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
+    const size_t smem = size_t(W) * point_fwd_warp_bytes<L, GRAD, TO>(P);
+    auto kern = point_fwd_kernel<L, GRAD, NORM, T, TO>;
+    cudaError_t err = ensure_smem(kern, smem);
+    if (err != cudaSuccess) return int(err);
+    const int64_t ntiles = ceil_div(a.n, P);
+    const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
+    const bool bulk = (reinterpret_cast<uintptr_t>(a.sph) % 16 == 0) &&
+                      (!GRAD || reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0);
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph), P, bulk ? 1 : 0);
+    return int(cudaGetLastError());
+}
+
+template <int L, bool NORM, bool DBW, typename T>
+int launch_point_bwd(const BwdArgs& a) {
+    static const PointTabs<L, T, DBW> tb = make_point_tabs<L, T, DBW>();
+    const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
+    const size_t smem = size_t(W) * ((DBW ? 3 : 2) * point_bwd_buf_bytes<L, T>(P) + 16);
+    auto kern = point_bwd_kernel<L, NORM, DBW, T>;
+    cudaError_t err = ensure_smem(kern, smem);
+    if (err != cudaSuccess) return int(err);
+    const int64_t ntiles = ceil_div(a.n, P);
+    const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
+    const bool bulk_in = reinterpret_cast<uintptr_t>(a.g) % 16 == 0;
+    const bool bulk_out = reinterpret_cast<uintptr_t>(a.grad_g) % 16 == 0;
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const T*>(a.xyz), static_cast<const T*>(a.g), static_cast<const T*>(a.v), a.n, tb,
+        static_cast<T*>(a.dxyz), static_cast<T*>(a.grad_g), static_cast<T*>(a.grad_xyz), P, bulk_in ? 1 : 0,
+        bulk_out ? 1 : 0, a.status);
+    return int(cudaGetLastError());
+}
+
+}  // namespace sph

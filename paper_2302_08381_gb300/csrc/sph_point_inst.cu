@@ -1,0 +1,48 @@
+// Instantiates the POINT kernels for one compile-time l_max. The build
+// compiles this file once per l_max in [0, SPH_MAX_L_POINT] with
+// -DSPH_INST_L=<l_max>, in parallel.
+#include "sph_point.cuh"
+
+#ifndef SPH_INST_L
+#error "compile with -DSPH_INST_L=<l_max>"
+#endif
+
+#define SPH_CAT2(a, b) a##b
+#define SPH_CAT(a, b) SPH_CAT2(a, b)
+
+namespace sph {
+
+int SPH_CAT(point_fwd_L, SPH_INST_L)(const FwdArgs& a) {
+    constexpr int L = SPH_INST_L;
+    const bool grad = a.dsph != nullptr;
+    const bool norm = a.normalized != 0;
+#define SPH_FWD(T, TO)                                                   \
+    return grad ? (norm ? launch_point_fwd<L, true, true, T, TO>(a)      \
+                        : launch_point_fwd<L, true, false, T, TO>(a))    \
+                : (norm ? launch_point_fwd<L, false, true, T, TO>(a)     \
+                        : launch_point_fwd<L, false, false, T, TO>(a));
+    if (a.dtype == SPH_F64) {
+        SPH_FWD(double, double)
+    }
+    if (a.out == SPH_OUT_BF16) {
+        SPH_FWD(float, __nv_bfloat16)
+    }
+    SPH_FWD(float, float)
+#undef SPH_FWD
+}
+
+int SPH_CAT(point_bwd_L, SPH_INST_L)(const BwdArgs& a) {
+    constexpr int L = SPH_INST_L;
+    if (a.dtype == SPH_F64)
+        return a.normalized ? launch_point_bwd<L, true, false, double>(a) : launch_point_bwd<L, false, false, double>(a);
+    return a.normalized ? launch_point_bwd<L, true, false, float>(a) : launch_point_bwd<L, false, false, float>(a);
+}
+
+int SPH_CAT(point_dbwd_L, SPH_INST_L)(const BwdArgs& a) {
+    constexpr int L = SPH_INST_L;
+    if (a.dtype == SPH_F64)
+        return a.normalized ? launch_point_bwd<L, true, true, double>(a) : launch_point_bwd<L, false, true, double>(a);
+    return a.normalized ? launch_point_bwd<L, true, true, float>(a) : launch_point_bwd<L, false, true, float>(a);
+}
+
+}  // namespace sph

@@ -26,3 +26,19 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Builds the CUDA library in-tree once if a fresh checkout lacks it."""
+    from paper_2302_08381_gb300 import _capi
+
+    if not os.path.exists(_capi.LIB_PATH):
+        from paper_2302_08381_gb300 import build
+
+        build.build()
+    yield

@@ -1,0 +1,166 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load, export every function the public header declares,
+produce host FP64 tables that agree with the closed forms, and reject bad
+arguments before touching any CUDA API.
+"""
+
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08381_gb300 import _capi as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(HEADER_DIR):
+        if f.endswith(".h"):
+            text = open(os.path.join(HEADER_DIR, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sphericart_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_loads_and_exports_header_symbols():
+    lib = C.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 10
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared) == set(C._PROTOS), "binding and header list different entry points"
+
+
+def test_version_and_limits():
+    assert C.sphericart_version() >= 10000
+    assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, C.SPH_KERNEL_POINT) == C.SPH_MAX_L_POINT
+    assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, C.SPH_KERNEL_SLICE) == C.SPH_MAX_L
+    assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_F64, C.SPH_KERNEL_POINT) == -1
+
+
+def _tri(l, m):
+    return l * (l + 1) // 2 + m
+
+
+def test_host_prefactor_table_matches_closed_form():
+    """Appendix C iteration (host, C++) vs Eq. Flm's closed form (oracle)."""
+    L = 128
+    F = C.sphericart_host_table(L, 0)
+    for l in range(L + 1):
+        for m in range(l + 1):
+            ref = oracle.prefactor(l, m)
+            assert F[_tri(l, m)] == pytest.approx(ref, rel=2e-13), (l, m)
+
+
+def test_host_recursion_coefficients():
+    L = 60
+    qll, a, b, e, fz, d = (C.sphericart_host_table(L, w) for w in (1, 2, 3, 4, 5, 6))
+    F = oracle.prefactor
+    s2 = 1 / math.sqrt(2)
+    for l in range(L + 1):
+        # Qtilde_l^l = F_l^l (-1)^l (2l-1)!!
+        dfact = 1
+        for k in range(1, 2 * l, 2):
+            dfact *= k
+        want = F(l, l) * (-1) ** l * float(dfact) if l < 150 else None
+        assert qll[_tri(l, l)] == pytest.approx(want, rel=1e-12)
+        if l >= 1:
+            assert d[_tri(l, l - 1)] == pytest.approx((2 * l - 1) * F(l, l - 1) / F(l - 1, l - 1), rel=1e-12)
+        for m in range(l + 1):
+            i = _tri(l, m)
+            sc = s2 if m == 0 else 1.0
+            if m <= l - 2:
+                assert a[i] == pytest.approx((2 * l - 1) / (l - m) * F(l, m) / F(l - 1, m), rel=1e-12)
+                assert b[i] == pytest.approx((l + m - 1) / (l - m) * F(l, m) / F(l - 2, m), rel=1e-12)
+                assert e[i] == pytest.approx(sc * F(l, m) / F(l - 1, m + 1), rel=1e-12)
+            else:
+                assert a[i] == 0 and b[i] == 0 and e[i] == 0
+            if m <= l - 1:
+                assert fz[i] == pytest.approx(sc * (l + m) * F(l, m) / F(l - 1, m), rel=1e-12)
+            else:
+                assert fz[i] == 0
+
+
+def _err(fn, *args):
+    with pytest.raises(C.SphericartError) as ei:
+        fn(*args)
+    return ei.value.code
+
+
+def test_argument_errors_before_any_cuda_call():
+    none = None
+    launch = None
+    # n < 0
+    assert _err(C.sphericart_compute_ex, 16, -1, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    # l_max out of range
+    assert _err(C.sphericart_compute_ex, 16, 4, -1, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 129, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    # bad enums
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 7, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 9, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 5, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 9, launch, 16, none, none, none) == C.SPH_EINVAL
+    # ddsph without dsph
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, 32, none) == C.SPH_EINVAL
+    # bf16 with FP64 arithmetic; POINT beyond its l_max, with Hessians, or mixed Q
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 1, 1, 0, 0, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 17, 0, 0, 0, 0, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 1, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 1, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    # NULL required pointers
+    assert _err(C.sphericart_compute_ex, none, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 0, launch, none, none, none, none) == C.SPH_EINVAL
+    # misaligned element pointers
+    assert _err(C.sphericart_compute_ex, 18, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
+    # backward / double backward
+    assert _err(C.sphericart_backward, 16, 16, -2, 6, 0, 0, 0, launch, 16, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_backward, 16, none, 4, 6, 0, 0, 0, launch, 16, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_backward, 16, 16, 4, 6, 0, 0, 0, launch, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, 1, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_double_backward, 16, 16, none, 4, 6, 0, 0, 0, launch, 16, 16, none) == C.SPH_EINVAL
+    # host table
+    with pytest.raises(C.SphericartError):
+        C.sphericart_host_table(200, 0)
+    assert "l_max" in C.last_error() or "host_table" in C.last_error()
+
+
+def test_zero_points_is_a_noop():
+    # n == 0 returns OK without a device and without touching pointers.
+    C.sphericart_compute_ex(None, 0, 8, 0, 0, 0, 0, 0, None, None, None, None, None)
+    C.sphericart_backward(None, None, 0, 8, 0, 0, 0, None, None, None)
+    C.sphericart_double_backward(None, None, None, 0, 8, 0, 0, 0, None, None, None, None)
+
+
+def test_compute_without_device_reports_cuda_error():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(C.SphericartError) as ei:
+        C.sphericart_compute_ex(16, 4, 8, 0, 0, 0, 0, 0, None, 16, None, None, None)
+    assert ei.value.code == C.SPH_ECUDA
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The tensor API rejects CPU tensors instead of computing elsewhere."""
+    import torch
+
+    from paper_2302_08381_gb300 import api
+
+    with pytest.raises(ValueError):
+        api.spherical_harmonics(torch.zeros(4, 3), 4)
+    # the package never imports the oracle
+    import paper_2302_08381_gb300 as pkg
+
+    src_dir = os.path.dirname(pkg.__file__)
+    for name in os.listdir(src_dir):
+        if name.endswith(".py"):
+            text = open(os.path.join(src_dir, name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name
