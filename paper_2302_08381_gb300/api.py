@@ -169,3 +169,67 @@ def materialized_backward(xyz, g, l_max, normalized=False, dsph=None):
 def device_status() -> int:
     """Reads and clears the device status word (nonzero: a bounded wait timed out)."""
     return C.sphericart_device_status()
+
+
+class BatchPlan:
+    """A ragged batch evaluated by one persistent launch (FP32, l_max <= 16).
+
+    ``xyz_list``: CUDA float32 tensors [n_s, 3]; ``lmax_list``: l_max per set.
+    Outputs are allocated here (``self.sph[s]`` [n_s, K_s], ``self.dsph[s]``
+    [n_s, 3, K_s] when ``gradients``) unless ``outputs`` supplies them.
+    ``execute()`` enqueues the launch on torch's current stream; it can be
+    captured in a CUDA graph.
+    """
+
+    def __init__(self, xyz_list, lmax_list, normalized=False, gradients=True, launch=None, outputs=None):
+        import ctypes
+
+        if len(xyz_list) != len(lmax_list) or not xyz_list:
+            raise ValueError("need one l_max per point set")
+        self.device = xyz_list[0].device
+        self.xyz = []
+        self.sph, self.dsph = [], []
+        arr = (C.sph_batch_set * len(xyz_list))()
+        for i, (x, L) in enumerate(zip(xyz_list, lmax_list)):
+            _check_points(x)
+            if x.dtype != torch.float32:
+                raise TypeError("batched sets are float32")
+            K = n_columns(int(L))
+            if outputs is not None:
+                s, d = outputs[i]
+            else:
+                s = torch.empty((x.shape[0], K), device=x.device)
+                d = torch.empty((x.shape[0], 3, K), device=x.device) if gradients else None
+            self.xyz.append(x)
+            self.sph.append(s)
+            self.dsph.append(d)
+            arr[i] = C.sph_batch_set(
+                x.data_ptr(), s.data_ptr(), d.data_ptr() if d is not None else None, x.shape[0], int(L),
+                1 if normalized else 0,
+            )
+        self._plan = ctypes.c_void_p()
+        C.check(
+            "sphericart_batch_plan_create",
+            C.lib().sphericart_batch_plan_create(arr, len(xyz_list), _launch(launch), ctypes.byref(self._plan)),
+        )
+
+    def execute(self):
+        C.check("sphericart_batch_execute", C.lib().sphericart_batch_execute(self._plan, _stream(self.device)))
+
+    def info(self):
+        import ctypes
+
+        p, t = ctypes.c_int64(), ctypes.c_int64()
+        C.check("sphericart_batch_plan_info", C.lib().sphericart_batch_plan_info(self._plan, ctypes.byref(p), ctypes.byref(t)))
+        return int(p.value), int(t.value)
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            C.lib().sphericart_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

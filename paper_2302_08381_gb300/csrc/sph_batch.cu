@@ -1,21 +1,334 @@
-// Ragged batches: placeholder entry points (replaced by the persistent batcher).
-#include "sph_internal.h"
+// Ragged batches in ONE persistent launch.
+//
+// Many point sets (e.g. the neighbour lists of many structures), each with its
+// own l_max <= SPH_MAX_L_POINT, are evaluated by a single kernel: every warp
+// pulls work tiles from a device counter, finds the tile's set by binary
+// search over the per-set tile prefix sums, and runs the POINT recursion for
+// that set's l_max (a switch over compile-time l_max). Tiles are sized per set
+// so that one tile's outputs fit a fixed shared-memory budget per warp: small
+// l_max sets get 32-point tiles, large ones fewer points (idle lanes cost
+// arithmetic, which is cheap here, not bandwidth). Sets are ordered by
+// decreasing l_max so the expensive tiles start first.
+//
+// The work list lives in device memory owned by the plan; executing the plan
+// is a counter reset plus one launch on the caller's stream, which can be
+// captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "sph_point.cuh"
+
+namespace sph {
+
+struct BatchSet {
+    const float* xyz;
+    float* sph;
+    float* dsph;
+    int64_t n;
+    int64_t tile_begin;  // prefix sum of tiles over the (sorted) sets
+    int32_t L;
+    int32_t P;           // points per tile for this set
+    int32_t norm;
+    int32_t bulk;        // outputs 16-byte aligned: bulk copies allowed
+};
+
+template <int K>
+struct BatchVis {
+    float* rv;
+    float* rd;  // nullptr: values only
+    float ux, uy, uz, ir;
+    int norm;
+    __device__ __forceinline__ void emit(int l, int k, Deriv<float> d) {
+        rv[k] = d.v;
+        if (rd) {
+            if (norm) normalize_deriv<false>(d, l, ux, uy, uz, ir);
+            rd[k] = d.gx;
+            rd[K + k] = d.gy;
+            rd[2 * K + k] = d.gz;
+        }
+    }
+};
+
+template <int L>
+__device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigned char* buf,
+                                           const PointTabs<16, float, false>& tb, int lane) {
+    constexpr int K = (L + 1) * (L + 1);
+    const int P = s.P;
+    const int64_t p0 = t * P;
+    const int cnt = int(min(int64_t(P), s.n - p0));
+    float* s_v = reinterpret_cast<float*>(buf);
+    float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * K * 4));
+    const bool grad = s.dsph != nullptr;
+    if (lane < cnt) {
+        const int64_t p = p0 + lane;
+        float x = s.xyz[3 * p], y = s.xyz[3 * p + 1], z = s.xyz[3 * p + 2];
+        float r2, ir = 1.f;
+        if (s.norm) {
+            unit_point(x, y, z, r2, ir);
+        } else {
+            r2 = x * x + y * y + z * z;
+        }
+        BatchVis<K> vis{s_v + size_t(lane) * K, grad ? s_d + size_t(lane) * 3 * K : nullptr, x, y, z, ir, s.norm};
+        // The l_max = 16 table holds every l <= 16 with the same layout
+        // prefix (entry (l, m) at l(l+1)/2 + m), so it serves every L.
+        point_core<L, true, false>(x, y, z, r2, tb, vis);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t ev = int64_t(cnt) * K;
+    int64_t ev_bulk = 0, ed_bulk = 0;
+    if (s.bulk) {
+        ev_bulk = (ev * 4) / 16 * 4;
+        ed_bulk = grad ? (3 * ev * 4) / 16 * 4 : 0;
+        if (lane == 0) {
+            if (ev_bulk) bulk_store(s.sph + p0 * K, s_v, uint32_t(ev_bulk * 4));
+            if (ed_bulk) bulk_store(s.dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * 4));
+            bulk_commit();
+        }
+    }
+    for (int64_t i = ev_bulk + lane; i < ev; i += 32) s.sph[p0 * K + i] = s_v[i];
+    if (grad)
+        for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) s.dsph[p0 * 3 * K + i] = s_d[i];
+    if (s.bulk && lane == 0) bulk_wait_read_all();
+    __syncwarp();
+}
+
+// Tables of Eq. iter-q / iter-deri for l <= 16, shared by every set.
+struct BatchTabs {
+    PointTabs<16, float, false> t;
+};
+
+__global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__ sets, int nsets,
+                                                    int64_t total_tiles, unsigned long long* __restrict__ counter,
+                                                    int per_warp_bytes, const __grid_constant__ BatchTabs tabs) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* buf = smem + size_t(warp) * per_warp_bytes;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= static_cast<unsigned long long>(total_tiles)) break;
+        // Binary search for the set holding tile t.
+        int lo = 0, hi = nsets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].tile_begin <= int64_t(t))
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchSet s = sets[lo];
+        const int64_t lt = int64_t(t) - s.tile_begin;
+        switch (s.L) {
+#define SPH_CASE(LL) \
+    case LL:         \
+        batch_tile<LL>(s, lt, buf, tabs.t, lane); \
+        break;
+            SPH_CASE(0) SPH_CASE(1) SPH_CASE(2) SPH_CASE(3) SPH_CASE(4) SPH_CASE(5) SPH_CASE(6) SPH_CASE(7)
+            SPH_CASE(8) SPH_CASE(9) SPH_CASE(10) SPH_CASE(11) SPH_CASE(12) SPH_CASE(13) SPH_CASE(14)
+            SPH_CASE(15) SPH_CASE(16)
+#undef SPH_CASE
+            default:
+                break;
+        }
+    }
+    if (lane == 0) bulk_wait_all();
+}
+
+}  // namespace sph
 
 using namespace sph;
 
+struct sph_batch_plan {
+    int device = -1;
+    int nsets = 0;
+    int64_t total_points = 0;
+    int64_t total_tiles = 0;
+    BatchSet* d_sets = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int warps_per_block = 1;
+    int blocks = 1;
+    int per_warp_bytes = 0;
+    size_t smem = 0;
+};
+
+namespace {
+
+const BatchTabs& batch_tabs() {
+    static const BatchTabs t{make_point_tabs<16, float, false>()};
+    return t;
+}
+
+int tile_mult4(int L) {
+    const int K = (L + 1) * (L + 1);
+    const int r = (K * 4) % 16;
+    return r == 0 ? 1 : 16 / (r == 8 ? 8 : 4);
+}
+
+}  // namespace
+
 extern "C" {
-int sphericart_batch_plan_create(const sph_batch_set*, int, const sph_launch*, sph_batch_plan** plan) {
-    if (plan) *plan = nullptr;
-    set_error("batched plans are not available in this build");
-    return SPH_EUNSUPPORTED;
+
+int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph_launch* launch,
+                                 sph_batch_plan** plan_out) {
+    if (!plan_out || !sets || nsets <= 0) {
+        set_error("batch_plan_create: sets, nsets > 0 and plan are required");
+        return SPH_EINVAL;
+    }
+    *plan_out = nullptr;
+    for (int i = 0; i < nsets; ++i) {
+        const sph_batch_set& s = sets[i];
+        if (s.n < 0 || s.l_max < 0 || s.l_max > SPH_MAX_L_POINT) {
+            set_error("batch set %d: n=%lld must be >= 0 and l_max=%d in [0,%d]", i, static_cast<long long>(s.n),
+                      s.l_max, SPH_MAX_L_POINT);
+            return SPH_EINVAL;
+        }
+        if (s.n > 0 && (!s.xyz || !s.sph)) {
+            set_error("batch set %d: xyz and sph must be non-NULL", i);
+            return SPH_EINVAL;
+        }
+        if ((reinterpret_cast<uintptr_t>(s.xyz) | reinterpret_cast<uintptr_t>(s.sph) |
+             reinterpret_cast<uintptr_t>(s.dsph)) % 4 != 0) {
+            set_error("batch set %d: buffers must be 4-byte aligned", i);
+            return SPH_EINVAL;
+        }
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch_plan_create: no usable CUDA device");
+        return SPH_ECUDA;
+    }
+    sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
+    const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
+    if (W > 8) {
+        set_error("warps_per_block=%d must be in [1,8]", W);
+        return SPH_EINVAL;
+    }
+    // Per-warp shared-memory budget: one 32-point l_max = 8 value+gradient tile.
+    const int budget = lau.points_per_tile > 0 ? lau.points_per_tile * 1296 : 32 * 1296;
+
+    std::vector<int> order(nsets);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].l_max > sets[b].l_max; });
+    std::vector<BatchSet> hs;
+    hs.reserve(nsets);
+    int64_t tiles = 0, points = 0;
+    int max_bytes = 0;
+    for (int oi : order) {
+        const sph_batch_set& s = sets[oi];
+        const int L = s.l_max;
+        const int K = (L + 1) * (L + 1);
+        const int grad = s.dsph ? 1 : 0;
+        const int row = K * 4 * (grad ? 4 : 1);
+        const int mult = tile_mult4(L);
+        int P = std::min(32, std::max(1, budget / row));
+        P = std::max(mult, P / mult * mult);
+        const int bytes = int(align16(size_t(P) * K * 4) + (grad ? align16(size_t(P) * 3 * K * 4) : 0));
+        max_bytes = std::max(max_bytes, bytes);
+        BatchSet b{};
+        b.xyz = s.xyz;
+        b.sph = s.sph;
+        b.dsph = s.dsph;
+        b.n = s.n;
+        b.tile_begin = tiles;
+        b.L = L;
+        b.P = P;
+        b.norm = s.normalized ? 1 : 0;
+        b.bulk = (reinterpret_cast<uintptr_t>(s.sph) % 16 == 0 && reinterpret_cast<uintptr_t>(s.dsph) % 16 == 0) ? 1 : 0;
+        tiles += (s.n + P - 1) / P;
+        points += s.n;
+        hs.push_back(b);
+    }
+    const size_t smem = size_t(W) * size_t(max_bytes);
+    if (smem > size_t(max_smem_optin())) {
+        set_error("batch plan needs %zu bytes of shared memory per block", smem);
+        return SPH_EINVAL;
+    }
+    auto* plan = new sph_batch_plan();
+    plan->device = dev;
+    plan->nsets = nsets;
+    plan->total_points = points;
+    plan->total_tiles = tiles;
+    plan->warps_per_block = W;
+    plan->per_warp_bytes = max_bytes;
+    plan->smem = smem;
+    if (cudaMalloc(&plan->d_sets, sizeof(BatchSet) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&plan->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(plan->d_sets);
+        delete plan;
+        set_error("batch plan: device allocation failed");
+        return SPH_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(plan->d_sets, hs.data(), sizeof(BatchSet) * hs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = ensure_smem(batch_kernel, smem);
+    if (e != cudaSuccess) {
+        cudaFree(plan->d_sets);
+        cudaFree(plan->d_counter);
+        delete plan;
+        set_error("batch plan: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(batch_kernel), 32 * W,
+                                                      smem) != cudaSuccess)
+        occ = 1;
+    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    const int64_t want = (tiles + W - 1) / W;
+    plan->blocks = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    *plan_out = plan;
+    return SPH_OK;
 }
-int sphericart_batch_execute(const sph_batch_plan*, void*) {
-    set_error("batched plans are not available in this build");
-    return SPH_EUNSUPPORTED;
+
+int sphericart_batch_execute(const sph_batch_plan* plan, void* stream) {
+    if (!plan) {
+        set_error("batch_execute: plan is NULL");
+        return SPH_EINVAL;
+    }
+    if (plan->total_tiles == 0) return SPH_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        set_error("batch_execute: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    batch_kernel<<<plan->blocks, 32 * plan->warps_per_block, plan->smem, st>>>(
+        plan->d_sets, plan->nsets, plan->total_tiles, plan->d_counter, plan->per_warp_bytes, batch_tabs());
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("batch_execute launch: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    return SPH_OK;
 }
-int sphericart_batch_plan_destroy(sph_batch_plan*) { return SPH_OK; }
-int sphericart_batch_plan_info(const sph_batch_plan*, int64_t*, int64_t*) {
-    set_error("batched plans are not available in this build");
-    return SPH_EUNSUPPORTED;
+
+int sphericart_batch_plan_destroy(sph_batch_plan* plan) {
+    if (!plan) return SPH_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (plan->device >= 0) cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->d_sets);
+    cudaFree(plan->d_counter);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete plan;
+    return SPH_OK;
 }
+
+int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points, int64_t* total_tiles) {
+    if (!plan) {
+        set_error("batch_plan_info: plan is NULL");
+        return SPH_EINVAL;
+    }
+    if (total_points) *total_points = plan->total_points;
+    if (total_tiles) *total_tiles = plan->total_tiles;
+    return SPH_OK;
 }
+
+}  // extern "C"

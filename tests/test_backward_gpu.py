@@ -1,0 +1,164 @@
+"""Fused recompute-backward and double backward against the oracle, central
+finite differences (FP64, h = 1e-3) and torch.autograd's own checks.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_08381_gb300 import _capi as C
+from paper_2302_08381_gb300 import api, inputs
+from paper_2302_08381_gb300.autograd import spherical_harmonics_autograd
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def _rel(got, ref):
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / (np.max(np.abs(ref)) + 1e-300))
+
+
+@pytest.mark.parametrize("kernel", ["point", "slice"])
+@pytest.mark.parametrize("normalized", [False, True])
+def test_backward_matches_oracle_every_lmax(kernel, normalized):
+    n = 1500 + 7
+    x = inputs.shell_points(n, 0.7, 3.0, seed=200).astype(np.float32).astype(np.float64)
+    for l_max in list(range(0, 17)) + ([20, 27] if kernel == "slice" else []):
+        K = (l_max + 1) ** 2
+        g = inputs.upstream(n, K, seed=201 + l_max).astype(np.float32).astype(np.float64)
+        dx = api.backward(_t(x), _t(g), l_max, normalized, kernel=kernel)
+        ref = oracle.backward(x, g, l_max, normalized)
+        assert _rel(dx.cpu().numpy(), ref) < 2e-5, l_max
+        # FP64 path
+        dx64 = api.backward(_t(x, torch.float64), _t(g, torch.float64), l_max, normalized, kernel=kernel)
+        assert _rel(dx64.cpu().numpy(), ref) < 1e-12, l_max
+
+
+def test_backward_equals_materialized_contraction():
+    n, l_max = 4099, 6
+    x = _t(inputs.shell_points(n, 0.7, 6.0, seed=202))
+    g = _t(inputs.upstream(n, 49, seed=203))
+    fused = api.backward(x, g, l_max)
+    plain = api.materialized_backward(x, g, l_max)
+    torch.cuda.synchronize()
+    assert _rel(fused.cpu().numpy(), plain.double().cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("kernel", ["point", "slice"])
+@pytest.mark.parametrize("normalized", [False, True])
+def test_double_backward_matches_oracle(kernel, normalized):
+    n = 700 + 3
+    x = inputs.shell_points(n, 0.7, 3.0, seed=204).astype(np.float64)
+    for l_max in (0, 1, 2, 3, 4, 6, 8, 12, 16):
+        K = (l_max + 1) ** 2
+        g = inputs.upstream(n, K, seed=205 + l_max).astype(np.float64)
+        v = inputs.upstream(n, 3, seed=305 + l_max).astype(np.float64)
+        rgg, rgx = oracle.double_backward(x, g, v, l_max, normalized)
+        gg, gx = api.double_backward(_t(x, torch.float64), _t(g, torch.float64), _t(v, torch.float64), l_max,
+                                     normalized, kernel=kernel)
+        assert _rel(gg.cpu().numpy(), rgg) < 1e-12, l_max
+        assert _rel(gx.cpu().numpy(), rgx) < 1e-7, l_max  # oracle Hessian is a Richardson difference
+        gg32, gx32 = api.double_backward(_t(x), _t(g), _t(v), l_max, normalized, kernel=kernel)
+        assert _rel(gg32.cpu().numpy(), rgg) < 1e-5 and _rel(gx32.cpu().numpy(), rgx) < 1e-4, l_max
+
+
+def test_hessian_output_slice():
+    """ddsph of the SLICE forward vs the oracle, plus exact invariants:
+    symmetric, trace-free (solid harmonics are harmonic), Euler relation."""
+    n = 300
+    x = inputs.shell_points(n, 0.7, 2.0, seed=206).astype(np.float64)
+    lv = None
+    for l_max in (0, 1, 2, 5, 9, 20):
+        sph, dsph, ddsph = api.spherical_harmonics(_t(x, torch.float64), l_max, gradients=True, hessians=True)
+        H = ddsph.cpu().numpy()
+        G = dsph.cpu().numpy()
+        ref = oracle.spherical_harmonics_hessian(x, l_max)
+        r = np.linalg.norm(x, axis=1)
+        lv = np.concatenate([np.full(2 * l + 1, l) for l in range(l_max + 1)])
+        hs = r[:, None] ** np.maximum(lv - 2, 0)[None, :] * (lv[None, :] + 1.0) ** 2.5
+        assert np.max(np.abs(H - ref) / hs[:, None, None, :]) < 1e-7, l_max
+        assert np.array_equal(H, H.transpose(0, 2, 1, 3))
+        assert np.max(np.abs(np.trace(H, axis1=1, axis2=2)) / hs) < 1e-11, l_max
+        euler = np.einsum("nj,nijk->nik", x, H) - (lv[None, None, :] - 1.0) * G
+        assert np.max(np.abs(euler) / hs[:, None, :]) < 1e-11, l_max
+        # normalized Hessians against the oracle
+        _, _, Hn = api.spherical_harmonics(_t(x, torch.float64), l_max, True, hessians=True)
+        refn = oracle.spherical_harmonics_hessian(x, l_max, True)
+        assert _rel(Hn.cpu().numpy(), refn) < 1e-7, l_max
+    del lv
+
+
+def test_autograd_gradcheck_fp64():
+    torch.manual_seed(0)
+    for l_max, normalized in ((3, False), (6, True), (8, False), (19, False)):
+        x = (torch.randn(16, 3, dtype=torch.float64, device=DEV) * 1.5).requires_grad_()
+        f = lambda p: spherical_harmonics_autograd(p, l_max, normalized)  # noqa: E731
+        assert torch.autograd.gradcheck(f, (x,), eps=1e-6, atol=1e-8, rtol=1e-6)
+        assert torch.autograd.gradgradcheck(f, (x,), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_backward_central_fd_fp64_h1e3():
+    """Config-3 distribution: dL/dxyz of L = sum(g * Y) vs central FD, h = 1e-3."""
+    n, l_max = 256, 6
+    x = inputs.shell_points(n, 0.7, 6.0, seed=207).astype(np.float64)
+    g = inputs.upstream(n, 49, seed=208).astype(np.float64)
+    dx = api.backward(_t(x, torch.float64), _t(g, torch.float64), l_max).cpu().numpy()
+    fd = np.zeros_like(x)
+    for j in range(3):
+        e = np.zeros_like(x)
+        e[:, j] = 1e-3
+        yp = api.spherical_harmonics(_t(x + e, torch.float64), l_max).cpu().numpy()
+        ym = api.spherical_harmonics(_t(x - e, torch.float64), l_max).cpu().numpy()
+        fd[:, j] = np.sum((yp - ym) * g, axis=1) / 2e-3
+    # FD truncation at h = 1e-3 for degree-6 polynomials with |r| <= 6
+    assert _rel(dx, fd) < 1e-5
+
+
+def test_workload_backward_full_size_sampled():
+    """N = 4,194,304 edge vectors, l_max = 6: fused backward at full size,
+    sampled against the oracle; equals the materialised contraction."""
+    n, l_max = 4_194_304, 6
+    x_np = inputs.shell_points(n, 0.7, 6.0, seed=3)
+    g_np = inputs.upstream(n, 49, seed=33)
+    x, g = _t(x_np), _t(g_np)
+    dx = api.backward(x, g, l_max)
+    plain = api.materialized_backward(x, g, l_max)
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(11).choice(n, 2048, replace=False)
+    idx = np.concatenate([idx, np.arange(n - 33, n)])
+    ref = oracle.backward(x_np[idx].astype(np.float64), g_np[idx].astype(np.float64), l_max)
+    assert _rel(dx.cpu().numpy()[idx], ref) < 2e-5
+    assert _rel(dx.cpu().numpy(), plain.double().cpu().numpy()) < 2e-5
+    v_np = inputs.upstream(n, 3, seed=34)
+    gg, gx = api.double_backward(x, g, _t(v_np), l_max)
+    torch.cuda.synchronize()
+    sub = idx[:256]
+    rgg, rgx = oracle.double_backward(x_np[sub].astype(np.float64), g_np[sub].astype(np.float64),
+                                      v_np[sub].astype(np.float64), l_max)
+    assert _rel(gg.cpu().numpy()[sub], rgg) < 2e-5 and _rel(gx.cpu().numpy()[sub], rgx) < 1e-4
+    assert api.device_status() == 0
+
+
+def test_backward_launch_shapes_and_unaligned():
+    n, l_max = 9001, 5
+    x_np = inputs.normal_points(n, seed=209).astype(np.float32)
+    g_np = inputs.upstream(n, 36, seed=210)
+    x = _t(x_np)
+    base = api.backward(x, _t(g_np), l_max, kernel="point")
+    for P in (4, 8, 16, 28, 32):
+        for W in (1, 3, 8):
+            d = api.backward(x, _t(g_np), l_max, kernel="point", launch=C.make_launch(P, W, 1, 0))
+            assert torch.equal(d, base)
+    # g at a 4-byte (not 16-byte) offset takes the plain-load path
+    gb = torch.empty(n * 36 + 1, device=DEV)
+    gb[1:] = _t(g_np).reshape(-1)
+    d = api.backward(x, gb[1:].view(n, 36), l_max, kernel="point")
+    assert torch.equal(d, base)
+    ref = oracle.backward(x_np.astype(np.float64), g_np.astype(np.float64), l_max)
+    assert _rel(base.cpu().numpy(), ref) < 2e-5

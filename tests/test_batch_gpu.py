@@ -1,0 +1,76 @@
+"""Ragged persistent batch: every set equals its own single-set launch
+(bitwise at equal tile sizes, else within FP32 rounding) and the oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_08381_gb300 import api, inputs
+from parity_utils import F32_GRAD, F32_VAL, assert_grads, assert_values
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _sets(nsets, choices, nmin, nmax, seed):
+    sizes, lmax, xyz = inputs.ragged_sets(nsets, choices, nmin, nmax, seed=seed)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xt = torch.from_numpy(xyz).to(DEV)
+    return [xt[offs[i]:offs[i + 1]] for i in range(nsets)], [int(v) for v in lmax], xyz, offs
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_batch_matches_single_launch_and_oracle(normalized):
+    xs, ls, xyz, offs = _sets(40, list(range(0, 17)), 1, 3000, seed=300)
+    plan = api.BatchPlan(xs, ls, normalized=normalized)
+    plan.execute()
+    torch.cuda.synchronize()
+    for i, (x, L) in enumerate(zip(xs, ls)):
+        v, g = api.spherical_harmonics(x, L, normalized, gradients=True)
+        torch.cuda.synchronize()
+        assert torch.allclose(plan.sph[i], v, rtol=0, atol=0) or torch.allclose(plan.sph[i], v, rtol=1e-6, atol=1e-6)
+        assert torch.allclose(plan.dsph[i], g, rtol=1e-6, atol=1e-6)
+        p = xyz[offs[i]:offs[i + 1]].astype(np.float64)
+        if p.shape[0]:
+            k = min(200, p.shape[0])
+            assert_values(plan.sph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_VAL)
+            assert_grads(plan.dsph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_GRAD)
+    n, t = plan.info()
+    assert n == sum(x.shape[0] for x in xs) and t > 0
+    plan.close()
+
+
+def test_batch_values_only_and_empty_sets():
+    xs, ls, xyz, offs = _sets(12, [3, 6, 8, 12], 1, 500, seed=301)
+    xs[3] = xs[3][:0]
+    plan = api.BatchPlan(xs, ls, gradients=False)
+    plan.execute()
+    torch.cuda.synchronize()
+    for i, (x, L) in enumerate(zip(xs, ls)):
+        assert plan.dsph[i] is None
+        if x.shape[0]:
+            ref = oracle.spherical_harmonics(x.double().cpu().numpy(), L)
+            assert_values(plan.sph[i].double().cpu().numpy(), x.double().cpu().numpy(), L, False, F32_VAL, ref=ref)
+
+
+def test_batch_graph_capture_replay():
+    xs, ls, _, _ = _sets(64, [3, 6, 8, 12], 1000, 20000, seed=302)
+    plan = api.BatchPlan(xs, ls)
+    plan.execute()
+    torch.cuda.synchronize()
+    want = [s.clone() for s in plan.sph]
+    for s in plan.sph:
+        s.zero_()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            plan.execute()
+    torch.cuda.current_stream().wait_stream(st)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(plan.sph, want):
+        assert torch.equal(a, b)

@@ -32,9 +32,13 @@ def _run(xyz_np, l_max, normalized, grad, kernel="auto", dtype=torch.float32, ou
         xyz, l_max, normalized, gradients=grad, out_dtype=out_dtype, qprec=qprec, kernel=kernel, launch=launch
     )
     torch.cuda.synchronize()
+
+    def host(t):
+        return (t.float() if t.dtype == torch.bfloat16 else t).double().cpu().numpy()
+
     if grad:
-        return res[0].float().double().cpu().numpy(), res[1].float().double().cpu().numpy()
-    return res.double().cpu().numpy() if res.dtype != torch.bfloat16 else res.float().double().cpu().numpy()
+        return host(res[0]), host(res[1])
+    return host(res)
 
 
 # --------------------------------------------------------------- small, every l_max
