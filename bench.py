@@ -234,6 +234,11 @@ def main():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
+    ap.add_argument(
+        "--profile",
+        choices=["fwd", "bwd", "dbwd", "batch"],
+        help="launch only this kernel family warmup+steps times (for ncu), print a short line",
+    )
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -244,6 +249,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile(args)
         return
 
     # CPU baseline first: the spawn pool is created before any CUDA call.
@@ -380,6 +388,50 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_profile(args):
+    """Minimal launches of one kernel family for profiler captures."""
+    import numpy as np
+    import torch
+
+    from paper_2302_08381_gb300 import _capi, api, inputs
+    from paper_2302_08381_gb300 import build as _build
+
+    if not os.path.exists(_capi.LIB_PATH):
+        _build.build()
+    dev = torch.device("cuda", 0)
+    n = args.n
+    if args.profile in ("fwd", "batch"):
+        L = L_MAX
+    else:
+        L = BWD_L
+    K = (L + 1) ** 2
+    x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).to(dev)
+    if args.profile == "fwd":
+        sph = torch.empty((n, K), device=dev)
+        dsph = torch.empty((n, 3, K), device=dev)
+        fn = lambda: api.spherical_harmonics(x, L, False, gradients=True, out=(sph, dsph))  # noqa: E731
+    elif args.profile in ("bwd", "dbwd"):
+        g = torch.from_numpy(inputs.upstream(n, K, seed=33)).to(dev)
+        v = torch.from_numpy(inputs.upstream(n, 3, seed=34)).to(dev)
+        dx = torch.empty_like(x)
+        if args.profile == "bwd":
+            fn = lambda: api.backward(x, g, L, out=dx)  # noqa: E731
+        else:
+            fn = lambda: api.double_backward(x, g, v, L)  # noqa: E731
+    else:
+        sizes, lmax, xyz = inputs.ragged_sets(512, [3, 6, 8, 12], 1000, 200_000, seed=5)
+        scale = n / float(sizes.sum())
+        sizes = np.maximum(1, (sizes * scale).astype(np.int64))
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        xt = torch.from_numpy(xyz[: offs[-1]]).to(dev)
+        plan = api.BatchPlan([xt[offs[i]:offs[i + 1]] for i in range(len(sizes))], [int(v) for v in lmax])
+        fn = plan.execute
+    for _ in range(args.warmup + args.steps):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "n": n, "launches": args.warmup + args.steps}), flush=True)
 
 
 def _events_ms(torch, stream, fn, reps, flush=None):

@@ -29,7 +29,8 @@ def value_scale(xyz, l_max, normalized):
     lv = lvec(l_max)
     if normalized:
         return np.ones((r.shape[0], lv.shape[0]))
-    return r[:, None] ** lv[None, :]
+    s = r[:, None] ** lv[None, :]
+    return np.where(s > 0, s, 1.0)  # r = 0: the exact values are 0 for l >= 1
 
 
 def grad_scale(xyz, l_max, normalized):

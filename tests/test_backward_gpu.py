@@ -19,9 +19,10 @@ def _t(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
 
 
-def _rel(got, ref):
+def _rel(got, ref, floor=0.0):
+    """max |got - ref| / max(max |ref|, floor)."""
     ref = np.asarray(ref, np.float64)
-    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / (np.max(np.abs(ref)) + 1e-300))
+    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / max(np.max(np.abs(ref)), floor, 1e-300))
 
 
 @pytest.mark.parametrize("kernel", ["point", "slice"])
@@ -55,17 +56,21 @@ def test_backward_equals_materialized_contraction():
 def test_double_backward_matches_oracle(kernel, normalized):
     n = 700 + 3
     x = inputs.shell_points(n, 0.7, 3.0, seed=204).astype(np.float64)
-    for l_max in (0, 1, 2, 3, 4, 6, 8, 12, 16):
+    lmaxes = (0, 1, 2, 3, 4, 6, 8, 12, 16) + ((20,) if kernel == "slice" else ())
+    for l_max in lmaxes:
         K = (l_max + 1) ** 2
         g = inputs.upstream(n, K, seed=205 + l_max).astype(np.float64)
         v = inputs.upstream(n, 3, seed=305 + l_max).astype(np.float64)
         rgg, rgx = oracle.double_backward(x, g, v, l_max, normalized)
         gg, gx = api.double_backward(_t(x, torch.float64), _t(g, torch.float64), _t(v, torch.float64), l_max,
                                      normalized, kernel=kernel)
+        # grad_xyz is exactly 0 for l_max <= 1 (linear harmonics); the oracle's
+        # difference quotient then returns rounding noise, hence the floor.
+        floor = 1e-6 * np.max(np.abs(g)) * np.max(np.abs(v))
         assert _rel(gg.cpu().numpy(), rgg) < 1e-12, l_max
-        assert _rel(gx.cpu().numpy(), rgx) < 1e-7, l_max  # oracle Hessian is a Richardson difference
+        assert _rel(gx.cpu().numpy(), rgx, floor) < 1e-7, l_max  # oracle Hessian is a Richardson difference
         gg32, gx32 = api.double_backward(_t(x), _t(g), _t(v), l_max, normalized, kernel=kernel)
-        assert _rel(gg32.cpu().numpy(), rgg) < 1e-5 and _rel(gx32.cpu().numpy(), rgx) < 1e-4, l_max
+        assert _rel(gg32.cpu().numpy(), rgg) < 1e-5 and _rel(gx32.cpu().numpy(), rgx, floor) < 1e-4, l_max
 
 
 def test_hessian_output_slice():
@@ -90,14 +95,17 @@ def test_hessian_output_slice():
         # normalized Hessians against the oracle
         _, _, Hn = api.spherical_harmonics(_t(x, torch.float64), l_max, True, hessians=True)
         refn = oracle.spherical_harmonics_hessian(x, l_max, True)
-        assert _rel(Hn.cpu().numpy(), refn) < 1e-7, l_max
+        assert _rel(Hn.cpu().numpy(), refn, 1e-3) < 1e-7, l_max
     del lv
 
 
 def test_autograd_gradcheck_fp64():
     torch.manual_seed(0)
     for l_max, normalized in ((3, False), (6, True), (8, False), (19, False)):
-        x = (torch.randn(16, 3, dtype=torch.float64, device=DEV) * 1.5).requires_grad_()
+        # unit-scale points keep r^l O(1), so difference quotients stay accurate
+        x = torch.randn(16, 3, dtype=torch.float64, device=DEV)
+        x = (x / x.norm(dim=1, keepdim=True) * (0.6 + 0.8 * torch.rand(16, 1, dtype=torch.float64, device=DEV)))
+        x = x.requires_grad_()
         f = lambda p: spherical_harmonics_autograd(p, l_max, normalized)  # noqa: E731
         assert torch.autograd.gradcheck(f, (x,), eps=1e-6, atol=1e-8, rtol=1e-6)
         assert torch.autograd.gradgradcheck(f, (x,), eps=1e-6, atol=1e-7, rtol=1e-5)

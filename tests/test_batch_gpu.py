@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2302_08381_gb300 import api, inputs
-from parity_utils import F32_GRAD, F32_VAL, assert_grads, assert_values
+from parity_utils import F32_GRAD, F32_VAL, assert_grads, assert_values, grad_scale, value_scale
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -29,9 +29,13 @@ def test_batch_matches_single_launch_and_oracle(normalized):
     for i, (x, L) in enumerate(zip(xs, ls)):
         v, g = api.spherical_harmonics(x, L, normalized, gradients=True)
         torch.cuda.synchronize()
-        assert torch.allclose(plan.sph[i], v, rtol=0, atol=0) or torch.allclose(plan.sph[i], v, rtol=1e-6, atol=1e-6)
-        assert torch.allclose(plan.dsph[i], g, rtol=1e-6, atol=1e-6)
         p = xyz[offs[i]:offs[i + 1]].astype(np.float64)
+        # Same recursion, separately compiled kernels: equal up to FP32
+        # rounding on the exact l-block scales.
+        if p.shape[0]:
+            dv = (plan.sph[i] - v).abs().double().cpu().numpy() / value_scale(p, L, normalized)
+            dg = (plan.dsph[i] - g).abs().double().cpu().numpy() / grad_scale(p, L, normalized)[:, None, :]
+            assert dv.max() < 1e-6 and dg.max() < 1e-6, (i, L, dv.max(), dg.max())
         if p.shape[0]:
             k = min(200, p.shape[0])
             assert_values(plan.sph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_VAL)
