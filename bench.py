@@ -54,21 +54,41 @@ def _oracle_chunk(args):
     return float(v.sum() + g.sum())
 
 
-def time_oracle(total_points: int, l_max: int, chunk: int = 16384):
-    """Times the FP64 oracle (values + gradients) over total_points on all host
-    cores with a spawn pool. Returns (points/s, cores, seconds)."""
-    import multiprocessing as mp
+class OraclePool:
+    """A spawn pool over all host cores running the FP64 oracle on chunks of
+    the benchmark distribution (values + gradients); workers return checksums
+    only, so nothing large crosses process boundaries."""
 
-    cores = os.cpu_count() or 1
-    nchunks = max(1, total_points // chunk)
-    work = [(chunk, 1000 + i, l_max) for i in range(nchunks)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_chunk, [(256, 1, l_max)] * cores)  # warm the workers
+    def __init__(self, l_max: int):
+        import multiprocessing as mp
+
+        self.l_max = l_max
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_chunk, [(256, 1, l_max)] * self.cores)  # import + warm every worker
+
+    def run(self, total_points: int, chunk: int = 16384, seed0: int = 1000):
+        nchunks = max(1, total_points // chunk)
+        work = [(chunk, seed0 + i, self.l_max) for i in range(nchunks)]
         t0 = time.perf_counter()
-        pool.map(_oracle_chunk, work, chunksize=1)
+        self.pool.map(_oracle_chunk, work, chunksize=1)
         dt = time.perf_counter() - t0
-    return nchunks * chunk / dt, cores, dt
+        return nchunks * chunk / dt, nchunks * chunk, dt
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def time_oracle(total_points: int, l_max: int, chunk: int = 16384):
+    """Times the FP64 oracle over total_points on all host cores.
+    Returns (points/s, cores, seconds)."""
+    op = OraclePool(l_max)
+    try:
+        vps, _, dt = op.run(total_points, chunk)
+    finally:
+        op.close()
+    return vps, op.cores, dt
 
 
 # ---------------------------------------------------------------- clocks
@@ -189,12 +209,16 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     sample = 131_072
-    cores = os.cpu_count() or 1
+    op = OraclePool(L_MAX)
+    cores = op.cores
     times = []
-    for i in range(args.warmup + args.steps):
-        vps, cores, dt = time_oracle(sample, L_MAX)
-        if i >= args.warmup:
-            times.append(dt)
+    try:
+        for i in range(args.warmup + args.steps):
+            _, pts, dt = op.run(sample, seed0=1000 + 97 * i)
+            if i >= args.warmup:
+                times.append(dt)
+    finally:
+        op.close()
     step = statistics.median(times)
     value = sample / step
     line = {

@@ -222,6 +222,37 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess,
 int sphericart_set_launch(int l_max, int dtype, int out, int grad,
                           const sph_launch* launch);
 
+/* ---------------------------------------------------------------- autotuner
+ * sphericart_autotune: times every valid POINT forward launch shape (points
+ * per tile, warps per block, blocks per SM) for this request on the caller's
+ * buffers (sph/dsph are overwritten), `reps` timed runs each (median, CUDA
+ * events on `stream`; synchronises), installs the fastest for later calls
+ * with launch == NULL (as sphericart_set_launch) and returns it in *best
+ * (and its time in *best_ms if non-NULL). l_max <= SPH_MAX_L_POINT, n > 0.
+ * The autotuner and the batch autotuner are the project's own: the paper
+ * grows its shared-memory allocation on first call instead (Section 3). */
+int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized,
+                        int dtype, int out, void* sph, void* dsph, void* stream,
+                        int reps, sph_launch* best, float* best_ms);
+
+/* sphericart_batch_autotune: times batch plans for these sets over a grid of
+ * per-warp shared-memory budgets, warps per block and blocks per SM, and
+ * returns the fastest shape for sphericart_batch_plan_create (for batch plans
+ * points_per_tile sets the per-warp budget as that many l_max = 8 FP32
+ * value+gradient rows of 1296 bytes).
+ * Overwrites the sets' outputs; synchronises. */
+int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream,
+                              int reps, sph_launch* best, float* best_ms);
+
+/* sphericart_tune_export: writes the tuned POINT shapes of the current device
+ * as text lines "gpu_name l_max dtype out grad P W B" into buf (NUL-terminated,
+ * truncated to len); *needed receives the full size. Host memory. */
+int sphericart_tune_export(char* buf, size_t len, size_t* needed);
+
+/* sphericart_tune_import: installs the lines of `text` whose gpu_name matches
+ * the current device (others are skipped); *imported receives the count. */
+int sphericart_tune_import(const char* text, int* imported);
+
 /* sphericart_version: library version as 10000*major + 100*minor + patch. */
 int sphericart_version(void);
 

@@ -80,6 +80,16 @@ _PROTOS = {
     "sphericart_launch_info": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(sph_launch)]),
     "sphericart_set_launch": (_I, [_I, _I, _I, _I, ctypes.POINTER(sph_launch)]),
     "sphericart_version": (_I, []),
+    "sphericart_autotune": (
+        _I,
+        [_P, _I64, _I, _I, _I, _I, _P, _P, _P, _I, ctypes.POINTER(sph_launch), ctypes.POINTER(ctypes.c_float)],
+    ),
+    "sphericart_batch_autotune": (
+        _I,
+        [ctypes.POINTER(sph_batch_set), _I, _P, _I, ctypes.POINTER(sph_launch), ctypes.POINTER(ctypes.c_float)],
+    ),
+    "sphericart_tune_export": (_I, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "sphericart_tune_import": (_I, [ctypes.c_char_p, ctypes.POINTER(_I)]),
 }
 
 _lib = None
@@ -175,6 +185,28 @@ def sphericart_set_launch(l_max, dtype, out, grad, launch: sph_launch):
 
 def sphericart_version() -> int:
     return lib().sphericart_version()
+
+
+def sphericart_autotune(xyz, n, l_max, normalized, dtype, out, sph, dsph, stream, reps=3):
+    best = sph_launch()
+    ms = ctypes.c_float(0)
+    _call("sphericart_autotune", xyz, n, l_max, normalized, dtype, out, sph, dsph, stream, reps, ctypes.byref(best),
+          ctypes.byref(ms))
+    return best, float(ms.value)
+
+
+def sphericart_tune_export() -> str:
+    need = ctypes.c_size_t(0)
+    _call("sphericart_tune_export", None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(max(1, need.value))
+    _call("sphericart_tune_export", buf, need.value, ctypes.byref(need))
+    return buf.value.decode()
+
+
+def sphericart_tune_import(text: str) -> int:
+    k = ctypes.c_int(0)
+    _call("sphericart_tune_import", text.encode(), ctypes.byref(k))
+    return int(k.value)
 
 
 def make_launch(points_per_tile=0, warps_per_block=0, blocks_per_sm=0, lanes_per_point=0):

@@ -195,6 +195,23 @@ bool resolve_point(sph_launch& s, const sph_launch& dflt, int L, int elem, size_
     return true;
 }
 
+}  // namespace
+
+bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s) {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_tuned.find(TuneKey{d, L, dtype, out, grad ? 1 : 0});
+    if (it == g_tuned.end()) return false;
+    *s = it->second;
+    return true;
+}
+
+namespace {
+
 bool valid_lanes(const sph_launch& s) {
     if (s.lanes_per_point != 0 && s.lanes_per_point != 8 && s.lanes_per_point != 16 && s.lanes_per_point != 32) {
         set_error("lanes_per_point=%d must be 0, 8, 16 or 32", s.lanes_per_point);

@@ -99,6 +99,10 @@ PointFwdFn point_fwd_fn(int L);
 PointBwdFn point_bwd_fn(int L);
 PointBwdFn point_dbwd_fn(int L);
 
+// Tuned POINT forward shape installed for (l_max, dtype, out, grad) on the
+// current device; false if none.
+bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s);
+
 // Bytes of one output row of the POINT forward for this request.
 size_t point_row_bytes(int L, int grad, int elem);
 

@@ -1,0 +1,225 @@
+// Autotuner for the POINT forward launch shape (points per tile, warps per
+// block, resident blocks per SM) and for ragged batch plans, timed on the
+// caller's own buffers with CUDA events; plus a text export/import of the
+// tuned table keyed by GPU name.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "sph_internal.h"
+
+using namespace sph;
+
+namespace {
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EventPair() {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+int tile_mult(int L, int elem) {
+    const int K = (L + 1) * (L + 1);
+    int r = (K * elem) % 16;
+    if (r == 0) return 1;
+    int g = 16;
+    while (r) {
+        const int t = g % r;
+        g = r;
+        r = t;
+    }
+    return 16 / g;
+}
+
+std::string device_name() {
+    int d = -1;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaGetDeviceProperties(&p, d) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string s = p.name;
+    for (char& c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, int dtype, int out, void* sph,
+                        void* dsph, void* stream, int reps, sph_launch* best, float* best_ms) {
+    if (!best || l_max < 0 || l_max > SPH_MAX_L_POINT || n <= 0 || !xyz || !sph) {
+        set_error("autotune: need n > 0, 0 <= l_max <= %d, xyz, sph and best", SPH_MAX_L_POINT);
+        return SPH_EINVAL;
+    }
+    if (reps <= 0) reps = 3;
+    const int elem = dtype == SPH_F64 ? 8 : (out == SPH_OUT_BF16 ? 2 : 4);
+    const int grad = dsph ? 1 : 0;
+    const int mult = tile_mult(l_max, elem);
+    const size_t row = point_row_bytes(l_max, grad, elem);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPair ev;
+    float best_t = 1e30f;
+    sph_launch best_s{0, 0, 0, 0};
+    const int Ps[] = {32, 28, 24, 20, 16, 12, 8, 4, 2, 1};
+    const int Ws[] = {1, 2, 4, 8};
+    const int Bs[] = {0, 1, 2, 3, 4, 6, 8};
+    for (int P : Ps) {
+        if (P % mult != 0) continue;
+        for (int W : Ws) {
+            const size_t smem = size_t(W) * (size_t(P) * row + 64);
+            if (smem > size_t(max_smem_optin())) continue;
+            for (int B : Bs) {
+                sph_launch s{P, W, B, 0};
+                int stt = sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE,
+                                                SPH_KERNEL_POINT, &s, sph, dsph, nullptr, stream);
+                if (stt != SPH_OK) {
+                    cudaGetLastError();
+                    continue;  // shape not launchable here (occupancy, limits)
+                }
+                std::vector<float> ts;
+                for (int r = 0; r < reps; ++r) {
+                    cudaEventRecord(ev.a, st);
+                    sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE, SPH_KERNEL_POINT, &s,
+                                          sph, dsph, nullptr, stream);
+                    cudaEventRecord(ev.b, st);
+                    if (cudaEventSynchronize(ev.b) != cudaSuccess) {
+                        set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                        return SPH_ECUDA;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev.a, ev.b);
+                    ts.push_back(ms);
+                }
+                std::sort(ts.begin(), ts.end());
+                const float t = ts[ts.size() / 2];
+                if (t < best_t) {
+                    best_t = t;
+                    best_s = s;
+                }
+            }
+        }
+    }
+    if (best_s.points_per_tile == 0) {
+        set_error("autotune: no launchable shape");
+        return SPH_EUNSUPPORTED;
+    }
+    *best = best_s;
+    if (best_ms) *best_ms = best_t;
+    return sphericart_set_launch(l_max, dtype, out, grad, &best_s);
+}
+
+int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream, int reps, sph_launch* best,
+                              float* best_ms) {
+    if (!best || !sets || nsets <= 0) {
+        set_error("batch_autotune: sets, nsets > 0 and best are required");
+        return SPH_EINVAL;
+    }
+    if (reps <= 0) reps = 3;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPair ev;
+    float best_t = 1e30f;
+    sph_launch best_s{0, 0, 0, 0};
+    // points_per_tile here scales the per-warp budget (in l_max = 8 gradient rows).
+    const int budgets[] = {32, 24, 16, 12, 8};
+    const int Ws[] = {1, 2, 4};
+    const int Bs[] = {0, 2, 3, 4};
+    for (int bud : budgets)
+        for (int W : Ws)
+            for (int B : Bs) {
+                sph_launch s{bud, W, B, 0};
+                sph_batch_plan* plan = nullptr;
+                if (sphericart_batch_plan_create(sets, nsets, &s, &plan) != SPH_OK) {
+                    cudaGetLastError();
+                    continue;
+                }
+                std::vector<float> ts;
+                bool ok = sphericart_batch_execute(plan, stream) == SPH_OK;
+                for (int r = 0; ok && r < reps; ++r) {
+                    cudaEventRecord(ev.a, st);
+                    ok = sphericart_batch_execute(plan, stream) == SPH_OK;
+                    cudaEventRecord(ev.b, st);
+                    ok = ok && cudaEventSynchronize(ev.b) == cudaSuccess;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev.a, ev.b);
+                    ts.push_back(ms);
+                }
+                sphericart_batch_plan_destroy(plan);
+                if (!ok || ts.empty()) continue;
+                std::sort(ts.begin(), ts.end());
+                const float t = ts[ts.size() / 2];
+                if (t < best_t) {
+                    best_t = t;
+                    best_s = s;
+                }
+            }
+    if (best_s.points_per_tile == 0) {
+        set_error("batch_autotune: no launchable shape");
+        return SPH_EUNSUPPORTED;
+    }
+    *best = best_s;
+    if (best_ms) *best_ms = best_t;
+    return SPH_OK;
+}
+
+int sphericart_tune_export(char* buf, size_t len, size_t* needed) {
+    std::ostringstream os;
+    const std::string name = device_name();
+    for (int L = 0; L <= SPH_MAX_L_POINT; ++L)
+        for (int dt = 0; dt <= 1; ++dt)
+            for (int out = 0; out <= 1; ++out)
+                for (int grad = 0; grad <= 1; ++grad) {
+                    if (dt == SPH_F64 && out == SPH_OUT_BF16) continue;
+                    int fam = 0;
+                    sph_launch s{0, 0, 0, 0};
+                    if (!tuned_launch(L, dt, out, grad, &s)) continue;
+                    (void)fam;
+                    os << name << ' ' << L << ' ' << dt << ' ' << out << ' ' << grad << ' ' << s.points_per_tile
+                       << ' ' << s.warps_per_block << ' ' << s.blocks_per_sm << '\n';
+                }
+    const std::string text = os.str();
+    if (needed) *needed = text.size() + 1;
+    if (buf && len > 0) {
+        const size_t k = std::min(len - 1, text.size());
+        std::memcpy(buf, text.data(), k);
+        buf[k] = '\0';
+    }
+    return SPH_OK;
+}
+
+int sphericart_tune_import(const char* text, int* imported) {
+    if (!text) {
+        set_error("tune_import: text is NULL");
+        return SPH_EINVAL;
+    }
+    std::istringstream is(text);
+    const std::string name = device_name();
+    std::string line;
+    int count = 0;
+    while (std::getline(is, line)) {
+        std::istringstream ls(line);
+        std::string gpu;
+        int L, dt, out, grad, P, W, B;
+        if (!(ls >> gpu >> L >> dt >> out >> grad >> P >> W >> B)) continue;
+        if (gpu != name) continue;
+        sph_launch s{P, W, B, 0};
+        if (sphericart_set_launch(L, dt, out, grad, &s) == SPH_OK) ++count;
+    }
+    if (imported) *imported = count;
+    return SPH_OK;
+}
+
+}  // extern "C"
