@@ -9,9 +9,11 @@ against the measured copy bandwidth.
 
 Also reported (separate keys): the fused recompute-backward against the
 materialise-then-contract backward (N = 4,194,304 edge vectors, |r| ~ U[0.7, 6],
-l_max = 6, upstream g ~ N(0,1)), both with their error against the FP64
-oracle on sampled points; the double backward; the end-to-end throughput from
-pinned host memory; and the FP64 oracle timed on the host cores.
+l_max = 6, upstream g ~ N(0,1)) with their mutual difference (both are checked
+against the FP64 oracle by the test suite); the double backward; the
+end-to-end throughput from pinned host memory; and the FP64 oracle timed on
+the host cores (the only legs that run the oracle are the CPU baseline and
+--impl reference).
 
 Multi-GPU: one process per GPU (torchrun); each rank evaluates its own N
 points (weak scaling, no collective on the data path); timing is the max
@@ -474,8 +476,6 @@ def _events_ms(torch, stream, fn, reps, flush=None):
 
 
 def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
-    import oracle
-
     out = {}
     # ---- end to end: pinned host xyz -> device -> compute -> pinned host outputs
     xyz_h = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).pin_memory()
@@ -541,24 +541,7 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     fused()
     dx_plain = plain()
     torch.cuda.synchronize()
-    rng = np.random.default_rng(5)
-    idx = rng.choice(BWD_N, 4096, replace=False)
-    ref = oracle.backward(xb_np[idx].astype(np.float64), gb_np[idx].astype(np.float64), Lb)
-    scale = np.max(np.abs(ref))
-    err_f = float(np.max(np.abs(dx.double().cpu().numpy()[idx] - ref)) / scale)
-    err_p = float(np.max(np.abs(dx_plain.double().cpu().numpy()[idx] - ref)) / scale)
-    # central differences in FP64 with h = 1e-3 on a few points, for context
-    sub = idx[:64]
-    xs = xb_np[sub].astype(np.float64)
-    gs = gb_np[sub].astype(np.float64)
-    fd = np.zeros_like(xs)
-    for j in range(3):
-        e = np.zeros_like(xs)
-        e[:, j] = 1e-3
-        fp = np.sum(oracle.spherical_harmonics(xs + e, Lb) * gs, axis=1)
-        fm = np.sum(oracle.spherical_harmonics(xs - e, Lb) * gs, axis=1)
-        fd[:, j] = (fp - fm) / 2e-3
-    err_fd = float(np.max(np.abs(dx.double().cpu().numpy()[sub] - fd)) / np.max(np.abs(fd)))
+    diff = float((dx.double() - dx_plain.double()).abs().max() / dx_plain.double().abs().max())
     bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
     out["backward"] = {
         "workload": f"N={BWD_N}, l_max={Lb}, |r|~U[0.7,6], g~N(0,1), FP32",
@@ -568,9 +551,9 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
         "fused_bwd_kernel_ms": t_bwd,
         "fused_bwd_achieved_GBs": bwd_bytes / (t_bwd * 1e-3) / 1e9,
         "double_backward_ms": t_dbwd,
-        "max_rel_err_vs_oracle_fused": err_f,
-        "max_rel_err_vs_oracle_plain": err_p,
-        "max_rel_err_vs_fd_h1e-3_fused": err_fd,
+        "max_rel_diff_fused_vs_plain": diff,
+        "stated_error": "both within 2e-5 (max-relative) of the FP64 oracle on sampled points of this "
+        "workload and within 1e-5 of central differences (h=1e-3, FP64): tests/test_backward_gpu.py",
     }
     return out
 
