@@ -183,6 +183,25 @@ int sphericart_batch_plan_destroy(sph_batch_plan* plan);
 int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points,
                                int64_t* total_tiles);
 
+/* sphericart_batch_compute_noalloc: evaluates a ragged batch like a plan does,
+ * in one persistent launch on `stream`, without allocating any device memory.
+ * It exists for callers that cannot call cudaMalloc -- code whose device
+ * memory is owned by a fixed arena or a framework allocator, or code that
+ * cannot afford the device synchronisation cudaMalloc implies. (The paper has
+ * no counterpart: its library allocates nothing of this kind.)
+ *   sets / nsets  as for sphericart_batch_plan_create (HOST array, read during
+ *                 the call only); at most 4096 sets, more returns SPH_EINVAL.
+ *   launch        NULL or a shape, as for sphericart_batch_plan_create.
+ * The work list and the tile counter live in a static device array of the
+ * library (about 225 KB on every GPU that loads it, held until exit). The
+ * first call on a device looks up that array's address (set-up); make that
+ * first call before any stream capture. Every call reuses the same array:
+ * the counter is cleared on each call, and calls whose work overlaps on the
+ * GPU (different streams, or host threads racing) race on it -- serialise
+ * them. Output buffers are the caller's, as everywhere. */
+int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int nsets,
+                                     const sph_launch* launch, void* stream);
+
 /* ----------------------------------------------------------------- services
  * sphericart_last_error: message of the last failed call on this thread
  * (static storage owned by the library; valid until the next call). */

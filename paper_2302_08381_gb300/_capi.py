@@ -73,6 +73,7 @@ _PROTOS = {
     "sphericart_batch_execute": (_I, [_P, _P]),
     "sphericart_batch_plan_destroy": (_I, [_P]),
     "sphericart_batch_plan_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "sphericart_batch_compute_noalloc": (_I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), _P]),
     "sphericart_last_error": (ctypes.c_char_p, []),
     "sphericart_max_l": (_I, [_I, _I, _I]),
     "sphericart_host_table": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),

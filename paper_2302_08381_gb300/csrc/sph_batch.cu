@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -332,3 +333,159 @@ int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------- no-allocation
+// A second way to run a ragged batch, for callers that cannot allocate
+// device memory: code running under a memory manager that owns every device
+// byte (a serving runtime with a fixed arena, a framework's caching
+// allocator that must not be bypassed), or code on a latency-critical path
+// where cudaMalloc's implicit device synchronisation is not acceptable.
+//
+// The work list and the tile counter live in the file-scope array below
+// instead of a plan's cudaMalloc'd buffers. Every GPU that loads this
+// library holds kNoAllocScratchBytes (about 225 KB) of it until the process
+// exits. All calls on a device share it and it keeps the last call's
+// contents; the counter is cleared on every call.
+namespace sph {
+namespace {
+
+constexpr int kNoAllocMaxSets = 4096;
+constexpr size_t kNoAllocCounterBytes = 256;  // counter, padded to keep the sets 256-byte aligned
+constexpr size_t kNoAllocScratchBytes = kNoAllocCounterBytes + sizeof(BatchSet) * kNoAllocMaxSets;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;                            // guards the two arrays below
+void* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+BatchSet g_noalloc_host[kNoAllocMaxSets];           // host staging of the work list
+
+}  // namespace
+}  // namespace sph
+
+extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int nsets, const sph_launch* launch,
+                                                void* stream) {
+    using namespace sph;
+    if (!sets || nsets <= 0) {
+        set_error("batch_compute_noalloc: sets and nsets > 0 are required");
+        return SPH_EINVAL;
+    }
+    if (nsets > kNoAllocMaxSets) {
+        set_error("batch_compute_noalloc: nsets=%d exceeds the static work-list capacity of %d sets", nsets,
+                  kNoAllocMaxSets);
+        return SPH_EINVAL;
+    }
+    for (int i = 0; i < nsets; ++i) {
+        const sph_batch_set& s = sets[i];
+        if (s.n < 0 || s.l_max < 0 || s.l_max > SPH_MAX_L_POINT) {
+            set_error("batch set %d: n=%lld must be >= 0 and l_max=%d in [0,%d]", i, static_cast<long long>(s.n),
+                      s.l_max, SPH_MAX_L_POINT);
+            return SPH_EINVAL;
+        }
+        if (s.n > 0 && (!s.xyz || !s.sph)) {
+            set_error("batch set %d: xyz and sph must be non-NULL", i);
+            return SPH_EINVAL;
+        }
+        if ((reinterpret_cast<uintptr_t>(s.xyz) | reinterpret_cast<uintptr_t>(s.sph) |
+             reinterpret_cast<uintptr_t>(s.dsph)) % 4 != 0) {
+            set_error("batch set %d: buffers must be 4-byte aligned", i);
+            return SPH_EINVAL;
+        }
+    }
+    const sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
+    const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
+    if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 32 || lau.blocks_per_sm < 0) {
+        set_error("batch_compute_noalloc: bad launch shape");
+        return SPH_EINVAL;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        set_error("batch_compute_noalloc: no usable CUDA device");
+        return SPH_ECUDA;
+    }
+    const int budget = lau.points_per_tile > 0 ? lau.points_per_tile * 1296 : 32 * 1296;
+
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    // Set-up, once per device, with that device current: the device address
+    // of the static array (host code must not use the symbol itself).
+    if (!g_noalloc_dev_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error("batch_compute_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return SPH_ECUDA;
+        }
+        g_noalloc_dev_ptr[dev] = p;
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
+    unsigned long long* d_counter = reinterpret_cast<unsigned long long*>(base);
+    BatchSet* d_sets = reinterpret_cast<BatchSet*>(base + kNoAllocCounterBytes);
+
+    // Work list in host staging: sets grouped by decreasing l_max (a
+    // counting sort, no allocation), tile prefix sums as in the plans.
+    int count[SPH_MAX_L_POINT + 2] = {0};
+    for (int i = 0; i < nsets; ++i) ++count[SPH_MAX_L_POINT - sets[i].l_max + 1];
+    for (int b = 1; b <= SPH_MAX_L_POINT + 1; ++b) count[b] += count[b - 1];
+    int64_t tiles = 0;
+    int max_bytes = 0;
+    for (int i = 0; i < nsets; ++i) {
+        const sph_batch_set& s = sets[i];
+        const int L = s.l_max;
+        const int K = (L + 1) * (L + 1);
+        const int grad = s.dsph ? 1 : 0;
+        const int row = K * 4 * (grad ? 4 : 1);
+        const int mult = tile_mult4(L);
+        int P = std::min(32, std::max(1, budget / row));
+        P = std::max(mult, P / mult * mult);
+        const int bytes = int(align16(size_t(P) * K * 4) + (grad ? align16(size_t(P) * 3 * K * 4) : 0));
+        max_bytes = std::max(max_bytes, bytes);
+        BatchSet& b = g_noalloc_host[count[SPH_MAX_L_POINT - L]++];
+        b = BatchSet{};
+        b.xyz = s.xyz;
+        b.sph = s.sph;
+        b.dsph = s.dsph;
+        b.n = s.n;
+        b.L = L;
+        b.P = P;
+        b.norm = s.normalized ? 1 : 0;
+        b.bulk = (reinterpret_cast<uintptr_t>(s.sph) % 16 == 0 && reinterpret_cast<uintptr_t>(s.dsph) % 16 == 0) ? 1 : 0;
+    }
+    for (int i = 0; i < nsets; ++i) {
+        g_noalloc_host[i].tile_begin = tiles;
+        tiles += (g_noalloc_host[i].n + g_noalloc_host[i].P - 1) / g_noalloc_host[i].P;
+    }
+    if (tiles == 0) return SPH_OK;
+    const size_t smem = size_t(W) * size_t(max_bytes);
+    if (smem > size_t(max_smem_optin())) {
+        set_error("batch_compute_noalloc: needs %zu bytes of shared memory per block", smem);
+        return SPH_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // From pageable host memory the copy has consumed g_noalloc_host when it
+    // returns, so the staging may be reused by the next call.
+    cudaError_t e = cudaMemcpyAsync(d_sets, g_noalloc_host, sizeof(BatchSet) * size_t(nsets), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = ensure_smem(batch_kernel, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch_compute_noalloc: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(batch_kernel), 32 * W,
+                                                      smem) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((tiles + W - 1) / W, int64_t(bps) * sm_count())));
+    batch_kernel<<<blocks, 32 * W, smem, st>>>(d_sets, nsets, tiles, d_counter, max_bytes, batch_tabs());
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("batch_compute_noalloc launch: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    return SPH_OK;
+}

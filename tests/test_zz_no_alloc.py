@@ -1,0 +1,86 @@
+"""The no-allocation batch entry point.
+
+Some callers cannot allocate device memory (their memory belongs to a fixed
+arena or a framework allocator, or they cannot afford the synchronisation a
+cudaMalloc implies). sphericart_batch_compute_noalloc serves them: it keeps
+its work list in a static device array of the library. This test calls it
+through the C-ABI twice in a row, with different batches, and checks both
+results against the plan-based batch entry point. It lives in its own file,
+collected last, and passes alone in a fresh process as well as after the
+rest of the suite.
+"""
+
+
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_08381_gb300 import _capi as C
+from paper_2302_08381_gb300 import api, inputs
+from parity_utils import grad_scale, value_scale
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _batch(nsets, choices, nmin, nmax, seed):
+    sizes, lmax, xyz = inputs.ragged_sets(nsets, choices, nmin, nmax, seed=seed)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xt = torch.from_numpy(xyz).to(DEV)
+    return [xt[offs[i]:offs[i + 1]] for i in range(nsets)], [int(v) for v in lmax], xyz, offs
+
+
+def _noalloc(xs, ls, normalized=False):
+    """Outputs allocated here by torch (the caller owns them), then one call."""
+    outs = []
+    arr = (C.sph_batch_set * len(xs))()
+    for i, (x, L) in enumerate(zip(xs, ls)):
+        K = (L + 1) ** 2
+        s = torch.full((x.shape[0], K), float("nan"), device=DEV)
+        d = torch.full((x.shape[0], 3, K), float("nan"), device=DEV)
+        outs.append((s, d))
+        arr[i] = C.sph_batch_set(x.data_ptr(), s.data_ptr(), d.data_ptr(), x.shape[0], L, 1 if normalized else 0)
+    code = C.lib().sphericart_batch_compute_noalloc(arr, len(xs), None, torch.cuda.current_stream().cuda_stream)
+    C.check("sphericart_batch_compute_noalloc", code)
+    return outs
+
+
+def _assert_close(outs, plan, xyz, offs, ls, normalized):
+    torch.cuda.synchronize()
+    for i, L in enumerate(ls):
+        s, d = outs[i]
+        p = xyz[offs[i]:offs[i + 1]].astype(np.float64)
+        if p.shape[0] == 0:
+            continue
+        dv = (s - plan.sph[i]).abs().double().cpu().numpy() / value_scale(p, L, normalized)
+        dg = (d - plan.dsph[i]).abs().double().cpu().numpy() / grad_scale(p, L, normalized)[:, None, :]
+        assert np.all(np.isfinite(dv)) and np.all(np.isfinite(dg)), i
+        assert dv.max() < 1e-6 and dg.max() < 1e-6, (i, L, dv.max(), dg.max())
+
+
+def test_noalloc_batch_matches_plan_on_two_calls_in_a_row():
+    xs1, ls1, xyz1, offs1 = _batch(48, [3, 6, 8, 12], 100, 20000, seed=500)
+    xs2, ls2, xyz2, offs2 = _batch(17, list(range(0, 17)), 1, 5000, seed=501)
+    plan1 = api.BatchPlan(xs1, ls1)
+    plan2 = api.BatchPlan(xs2, ls2, normalized=True)
+    plan1.execute()
+    plan2.execute()
+    out1 = _noalloc(xs1, ls1)
+    out2 = _noalloc(xs2, ls2, normalized=True)  # second call, different batch
+    _assert_close(out1, plan1, xyz1, offs1, ls1, False)
+    _assert_close(out2, plan2, xyz2, offs2, ls2, True)
+    plan1.close()
+    plan2.close()
+
+
+def test_noalloc_rejects_more_sets_than_the_static_capacity():
+    x = torch.zeros((1, 3), device=DEV)
+    s = torch.zeros((1, 1), device=DEV)
+    arr = (C.sph_batch_set * 4097)()
+    for i in range(4097):
+        arr[i] = C.sph_batch_set(x.data_ptr(), s.data_ptr(), None, 1, 0, 0)
+    code = C.lib().sphericart_batch_compute_noalloc(arr, 4097, None, torch.cuda.current_stream().cuda_stream)
+    assert code == C.SPH_EINVAL
+    assert "4096" in C.last_error()
+
