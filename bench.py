@@ -475,8 +475,93 @@ def _events_ms(torch, stream, fn, reps, flush=None):
     return statistics.median(times)
 
 
+def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
+    """512 ragged sets (sizes log-uniform in [1e3, 2e5], l_max from {3,6,8,12},
+    N(0,1) FP32 points), values + gradients: one persistent launch (eager and
+    replayed from a CUDA graph) vs one launch per set (eager and captured in
+    one graph)."""
+    sizes, lmax, xyz = inputs.ragged_sets(512, [3, 6, 8, 12], 1000, 200_000, seed=5)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xt = torch.from_numpy(xyz).to(dev)
+    xs = [xt[offs[i]:offs[i + 1]] for i in range(len(sizes))]
+    ls = [int(v) for v in lmax]
+    plan = api.BatchPlan(xs, ls)
+    outs = list(zip(plan.sph, plan.dsph))
+
+    def per_set():
+        for x, L, o in zip(xs, ls, outs):
+            api.spherical_harmonics(x, L, gradients=True, out=o)
+
+    plan.execute()
+    per_set()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    g_plan = torch.cuda.CUDAGraph()
+    g_sets = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g_plan, stream=side):
+            plan.execute()
+        with torch.cuda.graph(g_sets, stream=side):
+            per_set()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    total = int(sizes.sum())
+    nbytes = int(sum(s * (12 + 16 * (l + 1) ** 2) for s, l in zip(sizes, lmax)))
+    res = {
+        "workload": f"512 sets, {total} points, l_max from {{3,6,8,12}}, values+gradients FP32",
+        "points": total,
+        "algorithmic_bytes": nbytes,
+    }
+    for name, fn in (
+        ("persistent_launch", plan.execute),
+        ("persistent_graph", g_plan.replay),
+        ("per_set_launches", per_set),
+        ("per_set_graph", g_sets.replay),
+    ):
+        for _ in range(2):
+            fn()
+        ms = _events_ms(torch, stream, fn, 7, flush)
+        res[name + "_ms"] = ms
+        res[name + "_points_per_s"] = total / (ms * 1e-3)
+        res[name + "_GBs"] = nbytes / (ms * 1e-3) / 1e9
+    plan.close()
+    return res
+
+
+def run_variants_leg(torch, api, inputs, dev, stream, flush):
+    """Forward variants, each timed alone (median of 10 launches, L2 flushed)."""
+    res = {}
+    for n, L, label, kw, elem, ddims in (
+        (4_194_304, 8, "l8_values_only_f32", dict(), 4, 1),
+        (4_194_304, 8, "l8_grad_f32_normalized", dict(normalized=True, gradients=True), 4, 4),
+        (4_194_304, 8, "l8_grad_bf16_store", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
+        (4_194_304, 8, "l8_grad_f64", dict(gradients=True), 8, 4),
+        (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True), 4, 13),
+        (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 10, "l10_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
+    ):
+        dt = torch.float64 if elem == 8 else torch.float32
+        x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)
+        K = (L + 1) ** 2
+
+        def fn():
+            api.spherical_harmonics(x, L, **kw)
+
+        for _ in range(3):
+            fn()
+        ms = _events_ms(torch, stream, fn, 10, flush)
+        nbytes = n * (3 * (8 if elem == 8 else 4) + K * elem * ddims)
+        res[label] = {"n": n, "l_max": L, "ms": ms, "points_per_s": n / (ms * 1e-3),
+                      "achieved_GBs": nbytes / (ms * 1e-3) / 1e9}
+        del x
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     out = {}
+    out["variants"] = run_variants_leg(torch, api, inputs, dev, stream, flush)
     # ---- end to end: pinned host xyz -> device -> compute -> pinned host outputs
     xyz_h = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).pin_memory()
     sph_h = torch.empty((n, K), dtype=torch.float32).pin_memory()
@@ -542,6 +627,8 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     dx_plain = plain()
     torch.cuda.synchronize()
     diff = float((dx.double() - dx_plain.double()).abs().max() / dx_plain.double().abs().max())
+    del sb, db, gb, vb, xb, dx, dx_plain
+    out["batch"] = run_batch_leg(torch, np, api, inputs, dev, stream, flush)
     bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
     out["backward"] = {
         "workload": f"N={BWD_N}, l_max={Lb}, |r|~U[0.7,6], g~N(0,1), FP32",

@@ -57,11 +57,12 @@ template <int L>
 __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigned char* buf,
                                            const PointTabs<16, float, false>& tb, int lane) {
     constexpr int K = (L + 1) * (L + 1);
+    using RS = RowStride<L>;
     const int P = s.P;
     const int64_t p0 = t * P;
     const int cnt = int(min(int64_t(P), s.n - p0));
     float* s_v = reinterpret_cast<float*>(buf);
-    float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * K * 4));
+    float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * RS::V * 4));
     const bool grad = s.dsph != nullptr;
     if (lane < cnt) {
         const int64_t p = p0 + lane;
@@ -72,10 +73,17 @@ __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigne
         } else {
             r2 = x * x + y * y + z * z;
         }
-        BatchVis<K> vis{s_v + size_t(lane) * K, grad ? s_d + size_t(lane) * 3 * K : nullptr, x, y, z, ir, s.norm};
+        BatchVis<K> vis{s_v + size_t(lane) * RS::V, grad ? s_d + size_t(lane) * RS::D : nullptr, x, y, z, ir, s.norm};
         // The l_max = 16 table holds every l <= 16 with the same layout
         // prefix (entry (l, m) at l(l+1)/2 + m), so it serves every L.
         point_core<L, true, false>(x, y, z, r2, tb, vis);
+    }
+    if constexpr (RS::PAD) {  // even K: odd-stride rows, coalesced plain copy-out
+        __syncwarp();
+        warp_rows_out<K>(s.sph + p0 * K, s_v, cnt, RS::V, lane);
+        if (grad) warp_rows_out<3 * K>(s.dsph + p0 * 3 * K, s_d, cnt, RS::D, lane);
+        __syncwarp();
+        return;
     }
     fence_proxy_async_smem();
     __syncwarp();
@@ -226,11 +234,12 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         const int L = s.l_max;
         const int K = (L + 1) * (L + 1);
         const int grad = s.dsph ? 1 : 0;
-        const int row = K * 4 * (grad ? 4 : 1);
+        const int V = (K % 2 == 0) ? K + 1 : K, D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;  // smem row strides
+        const int row = 4 * (V + (grad ? D : 0));
         const int mult = tile_mult4(L);
         int P = std::min(32, std::max(1, budget / row));
         P = std::max(mult, P / mult * mult);
-        const int bytes = int(align16(size_t(P) * K * 4) + (grad ? align16(size_t(P) * 3 * K * 4) : 0));
+        const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
         max_bytes = std::max(max_bytes, bytes);
         BatchSet b{};
         b.xyz = s.xyz;
@@ -435,11 +444,12 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         const int L = s.l_max;
         const int K = (L + 1) * (L + 1);
         const int grad = s.dsph ? 1 : 0;
-        const int row = K * 4 * (grad ? 4 : 1);
+        const int V = (K % 2 == 0) ? K + 1 : K, D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;  // smem row strides
+        const int row = 4 * (V + (grad ? D : 0));
         const int mult = tile_mult4(L);
         int P = std::min(32, std::max(1, budget / row));
         P = std::max(mult, P / mult * mult);
-        const int bytes = int(align16(size_t(P) * K * 4) + (grad ? align16(size_t(P) * 3 * K * 4) : 0));
+        const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
         max_bytes = std::max(max_bytes, bytes);
         BatchSet& b = g_noalloc_host[count[SPH_MAX_L_POINT - L]++];
         b = BatchSet{};

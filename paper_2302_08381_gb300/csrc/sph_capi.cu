@@ -158,8 +158,9 @@ sph_launch default_point_fwd(int L, int grad, int elem) {
 
 sph_launch default_point_bwd(int L, int elem, int dbw) {
     const size_t K = size_t(L + 1) * (L + 1);
+    const size_t V = (K % 2 == 0) ? K + 1 : K;
     const int mult = tile_multiple(L, elem);
-    const size_t per_pt = K * elem * (dbw ? 3 : 2);
+    const size_t per_pt = V * elem * (dbw ? 3 : 2);
     const size_t budget = 48 * 1024;
     int P = 32;
     while (P > mult && size_t(P) * per_pt > budget) P -= mult;
@@ -395,7 +396,8 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
             return SPH_ENOMEM;
         }
         const size_t K = size_t(l_max + 1) * (l_max + 1);
-        if (!resolve_point(a.launch, default_point_bwd(l_max, e, dbw), l_max, e, K * e * (dbw ? 3 : 2)))
+        const size_t V = (K % 2 == 0) ? K + 1 : K;  // padded smem rows for even K
+        if (!resolve_point(a.launch, default_point_bwd(l_max, e, dbw), l_max, e, V * e * (dbw ? 3 : 2)))
             return SPH_EINVAL;
         PointBwdFn fn = dbw ? point_dbwd_fn(l_max) : point_bwd_fn(l_max);
         return cuda_status(fn(a), dbw ? "POINT double-backward launch" : "POINT backward launch");

@@ -130,7 +130,11 @@ __device__ __forceinline__ void normalize_deriv(Deriv<T>& d, int l, T ux, T uy, 
     d.gz = ir * (gz - uz * lv);
 }
 
-// Scale a point for the normalized form: u = xyz / r, r2 := |u|^2 (1, or 0 at r = 0).
+// Scale a point for the normalized form: u = xyz / r and r2 := |u|^2 as
+// computed from the rounded u (0 at r = 0). Taking |u|^2 rather than exactly
+// 1 keeps Q_l^m(z, r^2) the polynomial of the point u actually used; with
+// r^2 = 1 the O(eps) mismatch is amplified ~l^2 times by Eq. iter-q. The
+// chain rule of normalize_deriv is exact for any |u| (Euler's relation).
 template <typename T>
 __device__ __forceinline__ void unit_point(T& x, T& y, T& z, T& r2, T& ir) {
     const T rr = x * x + y * y + z * z;
@@ -139,7 +143,7 @@ __device__ __forceinline__ void unit_point(T& x, T& y, T& z, T& r2, T& ir) {
     x *= ir;
     y *= ir;
     z *= ir;
-    r2 = (rr > T(0)) ? T(1) : T(0);
+    r2 = x * x + y * y + z * z;
 }
 
 }  // namespace sph

@@ -7,10 +7,13 @@
 // (P <= 32, lanes >= P idle) from a persistent grid-stride loop. Outputs of a
 // tile are contiguous in global memory ([P, K] for sph, [P, 3, K] for dsph), so
 // lanes write their rows into a shared-memory image of that range and one lane
-// sends it with a bulk (TMA) copy; with K odd (even l_max) the row stride is
-// odd and the per-lane stores are bank-conflict free. Backward kernels read
-// their [P, K] upstream-gradient tile the same way, double buffered with
-// mbarrier-tracked bulk loads.
+// sends it with a bulk (TMA) copy. With K odd (even l_max) the row stride is
+// odd and the per-lane stores are bank-conflict free. With K even (odd l_max)
+// an image with stride K would put lanes on 4 to 32 times the same bank, so
+// rows are padded to an odd stride (K+1, 3K+1) and the warp copies the tile
+// out with coalesced plain stores instead. Backward kernels read their [P, K]
+// upstream-gradient tile the same way: bulk loads tracked by mbarriers,
+// double buffered (odd K), or coalesced plain loads into padded rows (even K).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -150,10 +153,43 @@ struct FwdVis {
     }
 };
 
+// Shared-memory row strides (elements) of a tile: the contiguous image for
+// odd K, odd-padded rows for even K.
+template <int L>
+struct RowStride {
+    static constexpr int K = (L + 1) * (L + 1);
+    static constexpr bool PAD = (K % 2 == 0);
+    static constexpr int V = PAD ? K + 1 : K;          // sph / g rows
+    static constexpr int D = PAD ? 3 * K + 1 : 3 * K;  // dsph rows
+};
+
 template <int L, bool GRAD, typename TO>
 __host__ __device__ constexpr size_t point_fwd_warp_bytes(int P) {
-    return align16(size_t(P) * (L + 1) * (L + 1) * sizeof(TO)) +
-           (GRAD ? align16(size_t(P) * 3 * (L + 1) * (L + 1) * sizeof(TO)) : 0);
+    return align16(size_t(P) * RowStride<L>::V * sizeof(TO)) +
+           (GRAD ? align16(size_t(P) * RowStride<L>::D * sizeof(TO)) : 0);
+}
+
+// Copies `rows` rows of `cols` elements from a padded shared-memory image
+// (row stride `stride`) to a contiguous global range, 32 consecutive
+// elements per warp store.
+template <int cols, typename TO>
+__device__ __forceinline__ void warp_rows_out(TO* __restrict__ gdst, const TO* __restrict__ ssrc, int rows, int stride,
+                                              int lane) {
+    const int total = rows * cols;
+    for (int i = lane; i < total; i += 32) {
+        const int r = i / cols;
+        gdst[i] = ssrc[r * stride + (i - r * cols)];
+    }
+}
+
+template <int cols, typename T>
+__device__ __forceinline__ void warp_rows_in(T* __restrict__ sdst, const T* __restrict__ gsrc, int rows, int stride,
+                                             int lane) {
+    const int total = rows * cols;
+    for (int i = lane; i < total; i += 32) {
+        const int r = i / cols;
+        sdst[r * stride + (i - r * cols)] = gsrc[i];
+    }
 }
 
 template <int L, bool GRAD, bool NORM, typename T, typename TO>
@@ -162,11 +198,12 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
                                                         TO* __restrict__ sph, TO* __restrict__ dsph, int P,
                                                         int bulk) {
     constexpr int K = (L + 1) * (L + 1);
+    using RS = RowStride<L>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
-    const size_t vbytes = align16(size_t(P) * K * sizeof(TO));
+    const size_t vbytes = align16(size_t(P) * RS::V * sizeof(TO));
     TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point_fwd_warp_bytes<L, GRAD, TO>(P));
     TO* s_d = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_v) + vbytes);
 
@@ -205,8 +242,15 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
             } else {
                 r2 = x * x + y * y + z * z;
             }
-            FwdVis<T, TO, GRAD, NORM, K> vis{s_v + size_t(lane) * K, s_d + size_t(lane) * 3 * K, x, y, z, ir};
+            FwdVis<T, TO, GRAD, NORM, K> vis{s_v + size_t(lane) * RS::V, s_d + size_t(lane) * RS::D, x, y, z, ir};
             point_core<L, GRAD, false>(x, y, z, r2, tb, vis);
+        }
+        if constexpr (RS::PAD) {
+            __syncwarp();
+            warp_rows_out<K>(sph + p0 * K, s_v, cnt, RS::V, lane);
+            if (GRAD) warp_rows_out<3 * K>(dsph + p0 * 3 * K, s_d, cnt, RS::D, lane);
+            __syncwarp();
+            continue;
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -280,7 +324,7 @@ struct DbwdVis {
 
 template <int L, typename T>
 __host__ __device__ constexpr size_t point_bwd_buf_bytes(int P) {
-    return align16(size_t(P) * (L + 1) * (L + 1) * sizeof(T));
+    return align16(size_t(P) * RowStride<L>::V * sizeof(T));
 }
 
 // DBW = false: backward (dxyz). DBW = true: double backward (grad_g, grad_xyz).
@@ -294,6 +338,9 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
                                                         T* __restrict__ grad_xyz, int P, int bulk_in,
                                                         int bulk_out, uint32_t* __restrict__ status) {
     constexpr int K = (L + 1) * (L + 1);
+    using RS = RowStride<L>;
+    if constexpr (RS::PAD) bulk_in = bulk_out = 0;  // padded rows: plain loads / stores
+    (void)bulk_out;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -359,7 +406,11 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
         if (failed) break;
         const int64_t eb_cur = cur ? eb1 : eb0;
         T* const gt = cur ? sg1 : sg0;
-        for (int64_t i = eb_cur + lane; i < int64_t(cnt) * K; i += 32) gt[i] = g[p0 * K + i];
+        if constexpr (RS::PAD) {
+            warp_rows_in<K>(gt, g + p0 * K, cnt, RS::V, lane);
+        } else {
+            for (int64_t i = eb_cur + lane; i < int64_t(cnt) * K; i += 32) gt[i] = g[p0 * K + i];
+        }
         __syncwarp();
         if (lane < cnt) {
             const int64_t p = p0 + lane;
@@ -371,7 +422,7 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
                 r2 = x * x + y * y + z * z;
             }
             if constexpr (!DBW) {
-                BwdVis<T, NORM, K> vis{gt + size_t(lane) * K, T(0), T(0), T(0), T(0)};
+                BwdVis<T, NORM, K> vis{gt + size_t(lane) * RS::V, T(0), T(0), T(0), T(0)};
                 point_core<L, true, false>(x, y, z, r2, tb, vis);
                 T ax = vis.ax, ay = vis.ay, az = vis.az;
                 if (NORM) {
@@ -383,8 +434,8 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
                 dxyz[3 * p + 1] = ay;
                 dxyz[3 * p + 2] = az;
             } else {
-                DbwdVis<T, NORM, K> vis{gt + size_t(lane) * K,
-                                        so + size_t(lane) * K,
+                DbwdVis<T, NORM, K> vis{gt + size_t(lane) * RS::V,
+                                        so + size_t(lane) * RS::V,
                                         v[3 * p],
                                         v[3 * p + 1],
                                         v[3 * p + 2],
@@ -404,7 +455,10 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
             }
         }
         if constexpr (DBW) {
-            if (grad_g) {
+            if (grad_g && RS::PAD) {
+                __syncwarp();
+                warp_rows_out<K>(grad_g + p0 * K, so, cnt, RS::V, lane);
+            } else if (grad_g) {
                 fence_proxy_async_smem();
                 __syncwarp();
                 const int64_t ev = int64_t(cnt) * K;

@@ -152,20 +152,22 @@ def test_empty_and_tiny():
                 assert_values(v, xyz.astype(np.float64), 6, False, F32_VAL)
 
 
-def test_launch_shapes_and_persistent_loop():
-    """Several tiles per warp (one CTA per SM), every tile size, ragged tail."""
+@pytest.mark.parametrize("l_max", [7, 8])
+def test_launch_shapes_and_persistent_loop(l_max):
+    """Several tiles per warp (one CTA per SM), every tile size, ragged tail;
+    l_max = 7 takes the padded-row path, l_max = 8 the bulk-copy path."""
     n = 20_011
     xyz = inputs.normal_points(n, seed=104).astype(np.float32)
-    ref = oracle.spherical_harmonics_grad(xyz.astype(np.float64), 8, False)
+    ref = oracle.spherical_harmonics_grad(xyz.astype(np.float64), l_max, False)
     base = None
     for P in (4, 8, 12, 16, 20, 24, 28, 32):
         for W in (1, 2, 4):
             lau = C.make_launch(P, W, 1, 0)
-            v, g = _run(xyz, 8, False, True, "point", launch=lau)
+            v, g = _run(xyz, l_max, False, True, "point", launch=lau)
             if base is None:
                 base = (v, g)
-                assert_values(v, xyz.astype(np.float64), 8, False, F32_VAL, ref=ref[0])
-                assert_grads(g, xyz.astype(np.float64), 8, False, F32_GRAD, ref=ref[1])
+                assert_values(v, xyz.astype(np.float64), l_max, False, F32_VAL, ref=ref[0])
+                assert_grads(g, xyz.astype(np.float64), l_max, False, F32_GRAD, ref=ref[1])
             else:
                 np.testing.assert_array_equal(v, base[0])
                 np.testing.assert_array_equal(g, base[1])
