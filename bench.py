@@ -540,6 +540,13 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True), 4, 13),
         (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
         (1_000_000, 10, "l10_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
+        # the paper's GPU table sizes (10k / 100k points, l_max = 8)
+        (10_000, 8, "l8_values_f64_n10k", dict(), 8, 1),
+        (10_000, 8, "l8_values_f64_n10k_normalized", dict(normalized=True), 8, 1),
+        (10_000, 8, "l8_grad_f32_n10k", dict(gradients=True), 4, 4),
+        (100_000, 8, "l8_values_f32_n100k", dict(), 4, 1),
+        (100_000, 8, "l8_grad_f32_n100k", dict(gradients=True), 4, 4),
+        (100_000, 8, "l8_grad_f64_n100k", dict(gradients=True), 8, 4),
     ):
         dt = torch.float64 if elem == 8 else torch.float32
         x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)
@@ -553,7 +560,7 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         ms = _events_ms(torch, stream, fn, 10, flush)
         nbytes = n * (3 * (8 if elem == 8 else 4) + K * elem * ddims)
         res[label] = {"n": n, "l_max": L, "ms": ms, "points_per_s": n / (ms * 1e-3),
-                      "achieved_GBs": nbytes / (ms * 1e-3) / 1e9}
+                      "ns_per_point": ms * 1e6 / n, "achieved_GBs": nbytes / (ms * 1e-3) / 1e9}
         del x
         torch.cuda.empty_cache()
     return res

@@ -69,8 +69,11 @@ typedef enum { SPH_F32 = 0, SPH_F64 = 1 } sph_dtype;
  * computed in FP32 and stored as bfloat16, round-to-nearest-even (uint16 bits). */
 typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
 
-/* Precision of the Q_l^m recursion (Eq. iter-q). SPH_Q_F64 with SPH_F32 runs the
- * Q recursion in FP64 and everything else in FP32 ("mixed"). */
+/* Internal precision. SPH_Q_F64 with SPH_F32 ("mixed") keeps FP32 inputs and
+ * outputs but runs the unit-vector scaling, the c_m/s_m (Eq. iter-sc) and
+ * Q_l^m (Eq. iter-q) recursions and the assembly in FP64, rounding once on
+ * store. Measured: FP32 error at high l_max comes from rounding u = xyz/r and
+ * the c_m/s_m powers, not from the Q recursion alone. SLICE kernels only. */
 typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
 /* Kernel family. AUTO picks POINT when l_max <= SPH_MAX_L_POINT and no Hessian

@@ -65,8 +65,9 @@ def spherical_harmonics(
     Returns ``sph`` [n, K]; with ``gradients`` also ``dsph`` [n, 3, K]; with
     ``hessians`` also ``ddsph`` [n, 3, 3, K]. ``normalized=False`` gives the
     scaled r^l Y_l^m. ``out_dtype=torch.bfloat16`` stores FP32 results as
-    bfloat16 (round to nearest even). ``qprec="f64"`` runs the Q recursion in
-    FP64 with FP32 everything else. ``out`` may supply preallocated outputs.
+    bfloat16 (round to nearest even). ``qprec="f64"`` keeps FP32 inputs and
+    outputs but computes in FP64 (unit vector, recursions, assembly).
+    ``out`` may supply preallocated outputs.
     """
     _check_points(xyz)
     dt = _dtype_code(xyz)

@@ -11,7 +11,7 @@
 // indexed by (l, m).
 //
 // This family covers large l_max, Hessians, and the mixed precision mode in
-// which the Q recursion runs in FP64 (TQ = double) and the rest in FP32.
+// which all arithmetic runs in FP64 (TQ = double) on FP32 inputs and outputs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,30 +38,52 @@ __device__ __forceinline__ TQ advance(const TQ* __restrict__ tb, int tn, int l, 
 // Visits every column of the lane's channels at one point. For each (l, m)
 // with m owned by this lane, calls f(l, k, Deriv) with normalized
 // derivatives when NORM.
+//
+// With TQ wider than T (the mixed mode) the unit-vector scaling and both
+// recursions (Eq. iter-sc, Eq. iter-q) run in TQ and only the assembled
+// outputs are rounded to T: in FP32 the dominant error is the rounding of
+// u = xyz/r and of the c_m/s_m powers (~l eps |Y|), not the Q recursion.
+// Rounds every field of a Deriv to T (identity when TQ == T).
+template <typename T, typename TQ>
+__device__ __forceinline__ Deriv<T> to_type(const Deriv<TQ>& d) {
+    Deriv<T> o;
+    o.v = T(d.v);
+    o.gx = T(d.gx);
+    o.gy = T(d.gy);
+    o.gz = T(d.gz);
+    o.hxx = T(d.hxx);
+    o.hxy = T(d.hxy);
+    o.hxz = T(d.hxz);
+    o.hyy = T(d.hyy);
+    o.hyz = T(d.hyz);
+    o.hzz = T(d.hzz);
+    return o;
+}
+
 template <typename TQ, typename T, bool GRAD, bool HESS, bool NORM, int G, typename F>
-__device__ __forceinline__ void slice_point(T x, T y, T z, int L, int j, const TQ* __restrict__ tb, int tn,
-                                            T inv_sqrt2, bool active, F&& f) {
-    T r2, ir = T(1);
+__device__ __forceinline__ void slice_point(T xin, T yin, T zin, int L, int j, const TQ* __restrict__ tb, int tn,
+                                            TQ inv_sqrt2, bool active, F&& f) {
+    TQ xq = TQ(xin), yq = TQ(yin), zq = TQ(zin);
+    TQ r2q, irq = TQ(1);
     if (NORM) {
-        unit_point(x, y, z, r2, ir);
+        unit_point(xq, yq, zq, r2q, irq);
     } else {
-        r2 = x * x + y * y + z * z;
+        r2q = xq * xq + yq * yq + zq * zq;
     }
-    const TQ zq = TQ(z), r2q = TQ(r2);
     for (int m0 = 0; m0 <= L; m0 += G) {
         const int m = m0 + j;
         // c_m, s_m and the two previous pairs by Eq. iter-sc.
-        T cm = T(1), sm = T(0), cm1 = T(0), sm1 = T(0), cm2 = T(0), sm2 = T(0);
+        TQ cq = TQ(1), sq = TQ(0), cq1 = TQ(0), sq1 = TQ(0), cq2 = TQ(0), sq2 = TQ(0);
         const int mt = min(m, L);
         for (int t = 1; t <= mt; ++t) {
-            const T nc = x * cm - y * sm;
-            const T ns = x * sm + y * cm;
-            cm2 = cm1;
-            sm2 = sm1;
-            cm1 = cm;
-            sm1 = sm;
-            cm = nc;
-            sm = ns;
+            const TQ nc = xq * cq - yq * sq;
+            const TQ ns = xq * sq + yq * cq;
+            cq2 = cq1;
+            sq2 = sq1;
+            cq1 = cq;
+            sq1 = sq;
+            cq = nc;
+            sq = ns;
         }
         TQ a1 = TQ(0), a2 = TQ(0), b1 = TQ(0), b2 = TQ(0), c1 = TQ(0), c2 = TQ(0);
         for (int l = m0; l <= L; ++l) {
@@ -70,34 +92,34 @@ __device__ __forceinline__ void slice_point(T x, T y, T z, int L, int j, const T
             const TQ qc = HESS ? advance(tb, tn, l, m + 2, zq, r2q, c1, c2) : TQ(0);
             if (active && m <= l) {
                 const int i = tri(l, m);
-                QParts<T> qp;
-                qp.Q = T(qa);
+                QParts<TQ> qp;
+                qp.Q = qa;
                 if (GRAD || HESS) {
-                    qp.E1 = T(tb[TE * tn + i] * b1);
-                    qp.Qz = T(tb[TFZ * tn + i] * a1);
+                    qp.E1 = tb[TE * tn + i] * b1;
+                    qp.Qz = tb[TFZ * tn + i] * a1;
                 } else {
-                    qp.E1 = qp.Qz = T(0);
+                    qp.E1 = qp.Qz = TQ(0);
                 }
                 if (HESS) {
-                    qp.G2 = T(tb[TG2 * tn + i] * c2);
-                    qp.G3 = T(tb[TG3 * tn + i] * b2);
-                    qp.G4 = T(tb[TG4 * tn + i] * a2);
+                    qp.G2 = tb[TG2 * tn + i] * c2;
+                    qp.G3 = tb[TG3 * tn + i] * b2;
+                    qp.G4 = tb[TG4 * tn + i] * a2;
                 } else {
-                    qp.G2 = qp.G3 = qp.G4 = T(0);
+                    qp.G2 = qp.G3 = qp.G4 = TQ(0);
                 }
                 if (m == 0) {
-                    Deriv<T> d = assemble_m0<GRAD, HESS>(qp, x, y, inv_sqrt2);
-                    if (NORM && (GRAD || HESS)) normalize_deriv<HESS>(d, l, x, y, z, ir);
-                    f(l, l * l + l, d);
+                    Deriv<TQ> d = assemble_m0<GRAD, HESS>(qp, xq, yq, inv_sqrt2);
+                    if (NORM && (GRAD || HESS)) normalize_deriv<HESS>(d, l, xq, yq, zq, irq);
+                    f(l, l * l + l, to_type<T>(d));
                 } else {
-                    Deriv<T> dc, ds;
-                    assemble_m<GRAD, HESS>(qp, x, y, T(m), T(m - 1), cm, sm, cm1, sm1, cm2, sm2, dc, ds);
+                    Deriv<TQ> dc, ds;
+                    assemble_m<GRAD, HESS>(qp, xq, yq, TQ(m), TQ(m - 1), cq, sq, cq1, sq1, cq2, sq2, dc, ds);
                     if (NORM && (GRAD || HESS)) {
-                        normalize_deriv<HESS>(dc, l, x, y, z, ir);
-                        normalize_deriv<HESS>(ds, l, x, y, z, ir);
+                        normalize_deriv<HESS>(dc, l, xq, yq, zq, irq);
+                        normalize_deriv<HESS>(ds, l, xq, yq, zq, irq);
                     }
-                    f(l, l * l + l + m, dc);
-                    f(l, l * l + l - m, ds);
+                    f(l, l * l + l + m, to_type<T>(dc));
+                    f(l, l * l + l - m, to_type<T>(ds));
                 }
             }
             a2 = a1;
@@ -112,7 +134,7 @@ __device__ __forceinline__ void slice_point(T x, T y, T z, int L, int j, const T
 
 template <typename TI, typename TQ, typename T, typename TO, bool GRAD, bool HESS, bool NORM, int G>
 __global__ void __launch_bounds__(256) slice_fwd_kernel(const TI* __restrict__ xyz, int64_t n, int L,
-                                                        const TQ* __restrict__ tb, int tn, T inv_sqrt2,
+                                                        const TQ* __restrict__ tb, int tn, TQ inv_sqrt2,
                                                         TO* __restrict__ sph, TO* __restrict__ dsph,
                                                         TO* __restrict__ ddsph) {
     constexpr int PPW = 32 / G;
@@ -252,7 +274,7 @@ int launch_fwd_g(const FwdArgs& a, const TQ* tb) {
     auto kern = slice_fwd_kernel<TI, TQ, T, TO, GRAD, HESS, NORM, G>;
     const int grid = slice_grid(kern, a.n, G, a.launch.blocks_per_sm);
     kern<<<grid, 256, 0, static_cast<cudaStream_t>(a.stream)>>>(
-        static_cast<const TI*>(a.xyz), a.n, a.l_max, tb, tri_size(SPH_MAX_L), T(host_tables().inv_sqrt2),
+        static_cast<const TI*>(a.xyz), a.n, a.l_max, tb, tri_size(SPH_MAX_L), TQ(host_tables().inv_sqrt2),
         static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph), static_cast<TO*>(a.ddsph));
     return int(cudaGetLastError());
 }

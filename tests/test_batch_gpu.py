@@ -30,12 +30,12 @@ def test_batch_matches_single_launch_and_oracle(normalized):
         v, g = api.spherical_harmonics(x, L, normalized, gradients=True)
         torch.cuda.synchronize()
         p = xyz[offs[i]:offs[i + 1]].astype(np.float64)
-        # Same recursion, separately compiled kernels: equal up to FP32
-        # rounding on the exact l-block scales.
+        # Same recursion, separately compiled kernels (different FMA
+        # contraction): equal up to a few FP32 roundings on the l-block scales.
         if p.shape[0]:
             dv = (plan.sph[i] - v).abs().double().cpu().numpy() / value_scale(p, L, normalized)
             dg = (plan.dsph[i] - g).abs().double().cpu().numpy() / grad_scale(p, L, normalized)[:, None, :]
-            assert dv.max() < 1e-6 and dg.max() < 1e-6, (i, L, dv.max(), dg.max())
+            assert dv.max() < 5e-6 and dg.max() < 5e-6, (i, L, dv.max(), dg.max())
         if p.shape[0]:
             k = min(200, p.shape[0])
             assert_values(plan.sph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_VAL)
