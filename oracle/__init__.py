@@ -18,4 +18,5 @@ from .sph_oracle import (  # noqa: F401
     backward,
     double_backward,
     column,
+    expansion,
 )

@@ -18,6 +18,8 @@ What it computes (arXiv 2302.08381, Section 2):
   of any order follow from Eq. iter-deri).
 * the adjoints used by autograd: ``dL/dxyz = sum_k g_k dY_k/dxyz`` and the double
   backward built on the Hessian.
+* the radial expansion of Eq. expansion, ``c_{nlm} = sum_k R_{nl}(r_k) Y_l^m(r_k)``
+  per centre, with the radial values given.
 
 This route deliberately does NOT use the Cartesian recursions the CUDA path is
 built on (Eqs. define-q, iter-q, iter-sc, iter-deri): it goes through theta and
@@ -62,6 +64,7 @@ __all__ = [
     "spherical_harmonics_hessian",
     "backward",
     "double_backward",
+    "expansion",
 ]
 
 
@@ -287,3 +290,24 @@ def double_backward(xyz, g, v, l_max: int, normalized: bool = False, hessian=Non
     grad_g = np.einsum("njk,nj->nk", grad, v)
     grad_xyz = np.einsum("nijk,nj,nk->ni", H, v, g)
     return grad_g, grad_xyz
+
+
+def expansion(xyz, radial, offsets, l_max: int, normalized: bool = False) -> np.ndarray:
+    """Eq. expansion per centre: c[i, n, (l,m)] = sum_k R[k, n, l] Y_l^m(x_k).
+
+    ``xyz`` [E, 3] are the points (edge vectors) grouped by centre, centre i
+    owning rows offsets[i]:offsets[i+1]; ``radial`` [E, n_rad, l_max+1] holds
+    R_nl evaluated at each point; Y is the scaled r^l Y_l^m (the paper absorbs
+    r^-l into R) or, with ``normalized``, Y_l^m. Returns [n_centres, n_rad, K].
+    """
+    Y = spherical_harmonics(xyz, l_max, normalized)
+    R = np.asarray(radial, dtype=np.float64)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    lv = np.concatenate([np.full(2 * l + 1, l) for l in range(l_max + 1)])
+    n_centres = offsets.shape[0] - 1
+    out = np.zeros((n_centres, R.shape[1], Y.shape[1]))
+    for i in range(n_centres):
+        a, b = offsets[i], offsets[i + 1]
+        if b > a:
+            out[i] = np.einsum("knl,kl->nl", R[a:b][:, :, lv], Y[a:b])
+    return out

@@ -443,3 +443,61 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not pins_pass()
     monkeypatch.undo()
     assert pins_pass()
+
+
+# --------------------------------------------------------------- expansion
+def _wigner_free_power_spectrum(c, l_max):
+    """p[i, n, n', l] = sum_m c[i, n, lm] c[i, n', lm]: invariant under rotations
+    of all points of a centre (each l block transforms by an orthogonal matrix)."""
+    out = []
+    for l in range(l_max + 1):
+        s = slice(l * l, (l + 1) ** 2)
+        out.append(np.einsum("inm,ikm->ink", c[:, :, s], c[:, :, s]))
+    return np.stack(out, axis=-1)
+
+
+def test_expansion_single_edge_and_linearity():
+    from oracle import expansion
+
+    l_max, nr = 5, 3
+    xyz = inputs.normal_points(7, seed=40)
+    R = inputs.upstream(7, nr * (l_max + 1), seed=41, dtype=np.float64).reshape(7, nr, l_max + 1)
+    offs = np.arange(8)  # one point per centre
+    c = expansion(xyz, R, offs, l_max)
+    Y = spherical_harmonics(xyz, l_max)
+    for l in range(l_max + 1):
+        s = slice(l * l, (l + 1) ** 2)
+        np.testing.assert_allclose(c[:, :, s], R[:, :, l][:, :, None] * Y[:, None, s], rtol=1e-14)
+    # one centre owning all points = sum of the single-point expansions
+    c_all = expansion(xyz, R, np.array([0, 7]), l_max)
+    np.testing.assert_allclose(c_all[0], c.sum(0), rtol=1e-13, atol=1e-14)
+    # empty centres give zeros
+    c_e = expansion(xyz, R, np.array([0, 0, 7, 7]), l_max)
+    assert np.all(c_e[0] == 0) and np.all(c_e[2] == 0)
+
+
+def test_expansion_power_spectrum_is_rotation_invariant():
+    from oracle import expansion
+
+    l_max, nr = 6, 4
+    rng = np.random.default_rng(42)
+    qm, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    xyz = inputs.shell_points(60, 0.8, 3.0, seed=43, dtype=np.float64)
+    r = np.linalg.norm(xyz, axis=1)
+    # radial values depend on r only, as a radial basis does
+    R = np.stack([np.stack([np.exp(-(r - n) ** 2) * (1 + l * r) for l in range(l_max + 1)], 1)
+                  for n in range(nr)], 1)
+    offs = np.array([0, 13, 13, 40, 60])
+    for normalized in (False, True):
+        p0 = _wigner_free_power_spectrum(expansion(xyz, R, offs, l_max, normalized), l_max)
+        p1 = _wigner_free_power_spectrum(expansion(xyz @ qm.T, R, offs, l_max, normalized), l_max)
+        np.testing.assert_allclose(p1, p0, rtol=1e-10, atol=1e-12)
+        # mixing l blocks (a plausible indexing slip) breaks the invariance
+        c = expansion(xyz, R, offs, l_max, normalized)
+        c_bad = c.copy()
+        c_bad[:, :, 4:9] = c[:, :, 4:9] + 0.3 * c[:, :, 0:1]
+        cr = expansion(xyz @ qm.T, R, offs, l_max, normalized)
+        cr_bad = cr.copy()
+        cr_bad[:, :, 4:9] = cr[:, :, 4:9] + 0.3 * cr[:, :, 0:1]
+        assert not np.allclose(_wigner_free_power_spectrum(c_bad, l_max),
+                               _wigner_free_power_spectrum(cr_bad, l_max), rtol=1e-6)
