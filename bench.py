@@ -566,6 +566,43 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
     return res
 
 
+def run_expansion_leg(torch, np, api, inputs, dev, stream, flush):
+    """Eq. expansion fused (harmonics never stored) vs materialised (forward
+    writes Y, torch contracts and sums per centre): 100,000 centres with
+    ~N(40, 10) points each, l_max = 6, 8 radial channels, FP32."""
+    l_max, nr, ncent = 6, 8, 100_000
+    rng = np.random.default_rng(610)
+    counts = np.clip(rng.normal(40, 10, size=ncent).round(), 0, 120).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    E = int(offs[-1])
+    x = torch.from_numpy(inputs.shell_points(E, 0.7, 5.0, seed=611)).to(dev)
+    R = torch.from_numpy(inputs.upstream(E, nr * (l_max + 1), seed=612)).to(dev).view(E, nr, l_max + 1)
+    o = torch.from_numpy(offs).to(dev)
+    c = torch.empty((ncent, nr, (l_max + 1) ** 2), device=dev)
+
+    def fused():
+        api.expansion(x, R, o, l_max, out=c)
+
+    def plain():
+        return api.materialized_expansion(x, R, o, l_max)
+
+    for _ in range(3):
+        fused()
+        plain()
+    t_f = _events_ms(torch, stream, fused, 10, flush)
+    t_p = _events_ms(torch, stream, plain, 5, flush)
+    nbytes = E * (12 + nr * (l_max + 1) * 4) + ncent * (8 + nr * (l_max + 1) ** 2 * 4)
+    return {
+        "workload": f"{ncent} centres, {E} points, l_max={l_max}, n_rad={nr}, FP32",
+        "fused_ms": t_f,
+        "materialized_ms": t_p,
+        "speedup": t_p / t_f,
+        "fused_points_per_s": E / (t_f * 1e-3),
+        "fused_achieved_GBs": nbytes / (t_f * 1e-3) / 1e9,
+        "algorithmic_bytes": nbytes,
+    }
+
+
 def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     out = {}
     out["variants"] = run_variants_leg(torch, api, inputs, dev, stream, flush)
@@ -636,6 +673,7 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     diff = float((dx.double() - dx_plain.double()).abs().max() / dx_plain.double().abs().max())
     del sb, db, gb, vb, xb, dx, dx_plain
     out["batch"] = run_batch_leg(torch, np, api, inputs, dev, stream, flush)
+    out["expansion"] = run_expansion_leg(torch, np, api, inputs, dev, stream, flush)
     bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
     out["backward"] = {
         "workload": f"N={BWD_N}, l_max={Lb}, |r|~U[0.7,6], g~N(0,1), FP32",

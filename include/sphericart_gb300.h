@@ -148,6 +148,23 @@ int sphericart_double_backward(const void* xyz, const void* g, const void* v,
                                int kernel, const sph_launch* launch,
                                void* grad_g, void* grad_xyz, void* stream);
 
+/* ---------------------------------------------------------------- expansion
+ * sphericart_expansion: the radial expansion of the paper's Eq. expansion,
+ * fused with the harmonics so that Y is never written to memory:
+ *   c[i, n, l*l+l+m] = sum_{k = offsets[i]}^{offsets[i+1]-1} R[k, n, l] * Y_l^m(x_k)
+ *   xyz      [n_points, 3]            points grouped by centre (device)
+ *   radial   [n_points, n_rad, l_max+1] R_nl at each point (device)
+ *   offsets  [n_centres + 1] int64    CSR offsets into the points (device)
+ *   c        [n_centres, n_rad, (l_max+1)^2] output (device)
+ *   normalized 0: Y is the scaled r^l Y_l^m (the paper folds r^-l into R),
+ *              1: Y_l^m on the unit sphere.  dtype: SPH_F32 or SPH_F64 for all.
+ * l_max <= SPH_MAX_L_POINT, 1 <= n_rad <= 64. A centre whose offsets are not
+ * non-decreasing within [0, n_points] gets zeros and sets bit 2 of the device
+ * status word (sphericart_device_status); nothing outside the buffers is read. */
+int sphericart_expansion(const void* xyz, const void* radial, const int64_t* offsets,
+                         int64_t n_centres, int64_t n_points, int n_rad, int l_max,
+                         int normalized, int dtype, void* c, void* stream);
+
 /* ------------------------------------------------------------------ batched
  * One set of a ragged batch: points xyz[n,3] f32 with their own l_max, outputs
  * sph[n,(l_max+1)^2] and dsph[n,3,(l_max+1)^2] (dsph may be NULL). Device

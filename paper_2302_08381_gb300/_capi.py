@@ -69,6 +69,7 @@ _PROTOS = {
         _I,
         [_P, _P, _P, _I64, _I, _I, _I, _I, ctypes.POINTER(sph_launch), _P, _P, _P],
     ),
+    "sphericart_expansion": (_I, [_P, _P, _P, _I64, _I64, _I, _I, _I, _I, _P, _P]),
     "sphericart_batch_plan_create": (_I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), ctypes.POINTER(_P)]),
     "sphericart_batch_execute": (_I, [_P, _P]),
     "sphericart_batch_plan_destroy": (_I, [_P]),
@@ -151,6 +152,12 @@ def sphericart_backward(xyz, g, n, l_max, normalized, dtype, kernel, launch, dxy
 def sphericart_double_backward(xyz, g, v, n, l_max, normalized, dtype, kernel, launch, grad_g, grad_xyz, stream):
     return _call(
         "sphericart_double_backward", xyz, g, v, n, l_max, normalized, dtype, kernel, launch, grad_g, grad_xyz, stream
+    )
+
+
+def sphericart_expansion(xyz, radial, offsets, n_centres, n_points, n_rad, l_max, normalized, dtype, c, stream):
+    return _call(
+        "sphericart_expansion", xyz, radial, offsets, n_centres, n_points, n_rad, l_max, normalized, dtype, c, stream
     )
 
 

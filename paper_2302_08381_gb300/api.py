@@ -167,6 +167,41 @@ def materialized_backward(xyz, g, l_max, normalized=False, dsph=None):
     return torch.einsum("nik,nk->ni", dsph, g)
 
 
+def expansion(xyz, radial, offsets, l_max, normalized=False, out=None):
+    """Eq. expansion per centre, fused: c[i, n, (l,m)] = sum_k R[k, n, l] Y_l^m(x_k).
+
+    ``xyz`` [E, 3] grouped by centre, ``radial`` [E, n_rad, l_max+1],
+    ``offsets`` int64 [n_centres+1] (CSR). Returns c [n_centres, n_rad, K].
+    """
+    _check_points(xyz)
+    radial = radial.contiguous()
+    offsets = offsets.contiguous()
+    if radial.dim() != 3 or radial.shape[0] != xyz.shape[0] or radial.shape[2] != l_max + 1:
+        raise ValueError("radial must be [n_points, n_rad, l_max+1]")
+    if radial.dtype != xyz.dtype or offsets.dtype != torch.int64 or not offsets.is_cuda:
+        raise ValueError("radial must match xyz's dtype; offsets must be a CUDA int64 tensor")
+    ncent = offsets.shape[0] - 1
+    nr = radial.shape[1]
+    c = torch.empty((ncent, nr, n_columns(l_max)), dtype=xyz.dtype, device=xyz.device) if out is None else out
+    C.sphericart_expansion(
+        xyz.data_ptr(), radial.data_ptr(), offsets.data_ptr(), ncent, xyz.shape[0], nr, l_max,
+        1 if normalized else 0, _dtype_code(xyz), c.data_ptr(), _stream(xyz.device),
+    )
+    return c
+
+
+def materialized_expansion(xyz, radial, offsets, l_max, normalized=False):
+    """Comparator: the harmonics written by the forward kernel, then the
+    contraction and the per-centre sum in torch (index_add)."""
+    Y = spherical_harmonics(xyz, l_max, normalized)
+    lv = torch.repeat_interleave(torch.arange(l_max + 1, device=xyz.device), 2 * torch.arange(l_max + 1, device=xyz.device) + 1)
+    counts = offsets[1:] - offsets[:-1]
+    centre = torch.repeat_interleave(torch.arange(offsets.shape[0] - 1, device=xyz.device), counts)
+    contrib = radial[:, :, lv] * Y[:, None, :]
+    out = torch.zeros((offsets.shape[0] - 1, radial.shape[1], Y.shape[1]), dtype=Y.dtype, device=xyz.device)
+    return out.index_add_(0, centre, contrib)
+
+
 def device_status() -> int:
     """Reads and clears the device status word (nonzero: a bounded wait timed out)."""
     return C.sphericart_device_status()
