@@ -487,6 +487,20 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
     ls = [int(v) for v in lmax]
     plan = api.BatchPlan(xs, ls)
     outs = list(zip(plan.sph, plan.dsph))
+    # the batch autotuner picks the per-warp budget, warps per block and CTAs per SM
+    import ctypes
+
+    from paper_2302_08381_gb300 import _capi as C
+
+    arr = (C.sph_batch_set * len(xs))()
+    for i, (x, L) in enumerate(zip(xs, ls)):
+        arr[i] = C.sph_batch_set(x.data_ptr(), plan.sph[i].data_ptr(), plan.dsph[i].data_ptr(), x.shape[0], L, 0)
+    best = C.sph_launch()
+    best_ms = ctypes.c_float()
+    C.check("sphericart_batch_autotune", C.lib().sphericart_batch_autotune(
+        arr, len(xs), stream.cuda_stream, 2, ctypes.byref(best), ctypes.byref(best_ms)))
+    plan.close()
+    plan = api.BatchPlan(xs, ls, launch=best, outputs=outs)
 
     def per_set():
         for x, L, o in zip(xs, ls, outs):
@@ -510,6 +524,8 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
     nbytes = int(sum(s * (12 + 16 * (l + 1) ** 2) for s, l in zip(sizes, lmax)))
     res = {
         "workload": f"512 sets, {total} points, l_max from {{3,6,8,12}}, values+gradients FP32",
+        "tuned_shape": {"budget_rows": best.points_per_tile, "warps_per_block": best.warps_per_block,
+                        "blocks_per_sm": best.blocks_per_sm},
         "points": total,
         "algorithmic_bytes": nbytes,
     }

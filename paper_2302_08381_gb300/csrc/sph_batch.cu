@@ -5,10 +5,11 @@
 // pulls work tiles from a device counter, finds the tile's set by binary
 // search over the per-set tile prefix sums, and runs the POINT recursion for
 // that set's l_max (a switch over compile-time l_max). Tiles are sized per set
-// so that one tile's outputs fit a fixed shared-memory budget per warp: small
-// l_max sets get 32-point tiles, large ones fewer points (idle lanes cost
-// arithmetic, which is cheap here, not bandwidth). Sets are ordered by
-// decreasing l_max so the expensive tiles start first.
+// so that one tile's outputs fill a fixed shared-memory budget per warp: small
+// l_max sets get up to 256-point tiles (each lane computes several points),
+// large ones fewer than 32 points (idle lanes cost arithmetic, which is cheap
+// here, not bandwidth). Sets are ordered by decreasing l_max so the expensive
+// tiles start first and warps mostly run the same l_max body together.
 //
 // The work list lives in device memory owned by the plan; executing the plan
 // is a counter reset plus one launch on the caller's stream, which can be
@@ -23,6 +24,8 @@
 #include "sph_point.cuh"
 
 namespace sph {
+
+constexpr int kBatchMaxTile = 256;  // points per batch tile (8 per lane)
 
 struct BatchSet {
     const float* xyz;
@@ -64,8 +67,10 @@ __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigne
     float* s_v = reinterpret_cast<float*>(buf);
     float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * RS::V * 4));
     const bool grad = s.dsph != nullptr;
-    if (lane < cnt) {
-        const int64_t p = p0 + lane;
+    // A tile may hold more than 32 points (small l_max): lane j computes the
+    // rows j, j+32, ... so that every set's tile fills the per-warp budget.
+    for (int row = lane; row < cnt; row += 32) {
+        const int64_t p = p0 + row;
         float x = s.xyz[3 * p], y = s.xyz[3 * p + 1], z = s.xyz[3 * p + 2];
         float r2, ir = 1.f;
         if (s.norm) {
@@ -73,7 +78,7 @@ __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigne
         } else {
             r2 = x * x + y * y + z * z;
         }
-        BatchVis<K> vis{s_v + size_t(lane) * RS::V, grad ? s_d + size_t(lane) * RS::D : nullptr, x, y, z, ir, s.norm};
+        BatchVis<K> vis{s_v + size_t(row) * RS::V, grad ? s_d + size_t(row) * RS::D : nullptr, x, y, z, ir, s.norm};
         // The l_max = 16 table holds every l <= 16 with the same layout
         // prefix (entry (l, m) at l(l+1)/2 + m), so it serves every L.
         point_core<L, true, false>(x, y, z, r2, tb, vis);
@@ -237,7 +242,7 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         const int V = (K % 2 == 0) ? K + 1 : K, D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;  // smem row strides
         const int row = 4 * (V + (grad ? D : 0));
         const int mult = tile_mult4(L);
-        int P = std::min(32, std::max(1, budget / row));
+        int P = std::min(kBatchMaxTile, std::max(1, budget / row));
         P = std::max(mult, P / mult * mult);
         const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
         max_bytes = std::max(max_bytes, bytes);
@@ -447,7 +452,7 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         const int V = (K % 2 == 0) ? K + 1 : K, D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;  // smem row strides
         const int row = 4 * (V + (grad ? D : 0));
         const int mult = tile_mult4(L);
-        int P = std::min(32, std::max(1, budget / row));
+        int P = std::min(kBatchMaxTile, std::max(1, budget / row));
         P = std::max(mult, P / mult * mult);
         const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
         max_bytes = std::max(max_bytes, bytes);
