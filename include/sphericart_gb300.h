@@ -124,6 +124,24 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
                           const sph_launch* launch,
                           void* sph, void* dsph, void* ddsph, void* stream);
 
+/* sphericart_compute_host: forward from HOST memory, end to end. Points are
+ * taken in chunks of `chunk_points` (0 = 1,048,576; rounded to a multiple of
+ * 32 and shrunk to fit) through a caller-provided DEVICE `workspace` of
+ * `workspace_bytes` (256-byte aligned; at least two chunk stages of
+ * xyz + sph (+ dsph)), and the host->device copy of chunk i+1, the kernel on
+ * chunk i and the device->host copy of chunk i-1 overlap on three streams the
+ * library owns (one set per device, created on first use). The work is
+ * ordered after everything already enqueued on `stream` and `stream` waits
+ * for its end; the call itself returns without synchronising. Host buffers
+ * should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to be
+ * asynchronous. Layouts, dtype and out as in sphericart_compute_ex (FP32 or
+ * FP64, optional bf16 store); no Hessians. Errors: SPH_EINVAL for bad sizes,
+ * NULL pointers or a workspace too small for two 32-point stages. */
+int sphericart_compute_host(const void* xyz_host, int64_t n, int l_max, int normalized,
+                            int dtype, int out, void* sph_host, void* dsph_host,
+                            void* workspace, size_t workspace_bytes,
+                            int64_t chunk_points, void* stream);
+
 /* ----------------------------------------------------------------- backward
  * sphericart_backward: fused recompute-backward (adjoint of the forward values).
  *   dxyz[n, i] = sum_k g[n, k] * d sph[n, k] / d x_i

@@ -64,6 +64,7 @@ _I64 = ctypes.c_int64
 _PROTOS = {
     "sphericart_compute": (_I, [_P, _I64, _I, _I, _P, _P, _P, _P]),
     "sphericart_compute_ex": (_I, [_P, _I64, _I, _I, _I, _I, _I, _I, ctypes.POINTER(sph_launch), _P, _P, _P, _P]),
+    "sphericart_compute_host": (_I, [_P, _I64, _I, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "sphericart_backward": (_I, [_P, _P, _I64, _I, _I, _I, _I, ctypes.POINTER(sph_launch), _P, _P]),
     "sphericart_double_backward": (
         _I,
@@ -143,6 +144,12 @@ def sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, qprec, kernel, 
     return _call(
         "sphericart_compute_ex", xyz, n, l_max, normalized, dtype, out, qprec, kernel, launch, sph, dsph, ddsph, stream
     )
+
+
+def sphericart_compute_host(xyz_host, n, l_max, normalized, dtype, out, sph_host, dsph_host, workspace,
+                            workspace_bytes, chunk_points, stream):
+    return _call("sphericart_compute_host", xyz_host, n, l_max, normalized, dtype, out, sph_host, dsph_host,
+                 workspace, workspace_bytes, chunk_points, stream)
 
 
 def sphericart_backward(xyz, g, n, l_max, normalized, dtype, kernel, launch, dxyz, stream):

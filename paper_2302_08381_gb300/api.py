@@ -110,6 +110,37 @@ def spherical_harmonics(
     return sph
 
 
+def spherical_harmonics_host(xyz, l_max, normalized=False, gradients=False, out=None, workspace=None,
+                             chunk_points=0, device=None):
+    """Forward from host tensors, pipelined in chunks through a device
+    workspace (host->device copy, kernel and device->host copy overlap).
+
+    ``xyz``: CPU tensor [n, 3] (pinned for asynchronous copies). Outputs are
+    pinned CPU tensors (allocated here unless ``out`` gives them). Returns
+    after the copies are enqueued on the current stream of ``device``; call
+    torch.cuda.synchronize() (or sync that stream) before reading them.
+    """
+    if xyz.is_cuda or xyz.dim() != 2 or xyz.shape[1] != 3 or not xyz.is_contiguous():
+        raise ValueError("xyz must be a contiguous CPU tensor [n, 3]")
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n, K = xyz.shape[0], n_columns(l_max)
+    if out is None:
+        sph = torch.empty((n, K), dtype=xyz.dtype, pin_memory=True)
+        dsph = torch.empty((n, 3, K), dtype=xyz.dtype, pin_memory=True) if gradients else None
+    else:
+        sph, dsph = out
+    if workspace is None:
+        chunk = chunk_points or (1 << 20)
+        per = xyz.element_size() * (3 + K * (4 if gradients else 1))
+        workspace = torch.empty(2 * (min(chunk, max(n, 32)) + 32) * per + 4096, dtype=torch.uint8, device=device)
+    C.sphericart_compute_host(
+        xyz.data_ptr(), n, l_max, 1 if normalized else 0, _dtype_code(xyz), C.SPH_OUT_SAME,
+        sph.data_ptr(), dsph.data_ptr() if dsph is not None else None,
+        workspace.data_ptr(), workspace.numel(), chunk_points, _stream(device),
+    )
+    return (sph, dsph) if gradients else sph
+
+
 def backward(xyz, g, l_max, normalized=False, kernel="auto", launch=None, out=None):
     """Fused recompute-backward: dxyz[n, i] = sum_k g[n, k] d sph[n, k] / d x_i."""
     _check_points(xyz)

@@ -48,7 +48,7 @@ def _units():
     units = []
     for l in range(MAX_L_POINT + 1):
         units.append(("sph_point_inst.cu", f"point_L{l}.o", [f"-DSPH_INST_L={l}"]))
-    for src in ("sph_slice.cu", "sph_capi.cu", "sph_batch.cu", "sph_tune.cu", "sph_expansion.cu", "sph_tables.cpp", "sph_point_registry.cpp"):
+    for src in ("sph_slice.cu", "sph_capi.cu", "sph_batch.cu", "sph_tune.cu", "sph_expansion.cu", "sph_host.cu", "sph_tables.cpp", "sph_point_registry.cpp"):
         units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units
 

@@ -122,11 +122,14 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* buf = smem + size_t(warp) * per_warp_bytes;
+    // The next tile index is fetched one tile ahead, so the atomic's round
+    // trip overlaps the current tile's work.
+    unsigned long long nxt = 0;
+    if (lane == 0) nxt = atomicAdd(counter, 1ull);
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        const unsigned long long t = __shfl_sync(0xffffffffu, nxt, 0);
         if (t >= static_cast<unsigned long long>(total_tiles)) break;
+        if (lane == 0) nxt = atomicAdd(counter, 1ull);
         // Binary search for the set holding tile t.
         int lo = 0, hi = nsets - 1;
         while (lo < hi) {

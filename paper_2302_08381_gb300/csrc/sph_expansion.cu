@@ -33,12 +33,16 @@ __device__ __forceinline__ int l_of_column(int k) {
     return l;
 }
 
+// Radial channels per point are staged as [l][n] with n padded to a multiple
+// of 4 (zeros), so the kExpansionAcc factors a column needs are contiguous
+// and 16-byte aligned.
+__host__ __device__ constexpr int padded_rad(int nr) { return (nr + 3) / 4 * 4; }
+
 template <int L, typename T>
 __host__ __device__ constexpr size_t expansion_warp_bytes(int nr) {
     constexpr int K = (L + 1) * (L + 1);
     constexpr int SY = (K % 2 == 0) ? K + 1 : K;
-    const int RW = nr * (L + 1);
-    const int SR = (RW % 2 == 0) ? RW + 1 : RW;
+    const int SR = (L + 1) * padded_rad(nr) + 4;  // row stride, a multiple of 4 (16-byte rows)
     return align16(size_t(32) * SY * sizeof(T)) + align16(size_t(32) * SR * sizeof(T)) +
            align16(size_t(nr) * K * sizeof(T));
 }
@@ -52,8 +56,9 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     constexpr int K = (L + 1) * (L + 1);
     constexpr int SY = (K % 2 == 0) ? K + 1 : K;
     constexpr int RL = L + 1;
-    const int RW = nr * RL;
-    const int SR = (RW % 2 == 0) ? RW + 1 : RW;
+    const int NP = padded_rad(nr);
+    const int RW = nr * RL;            // R row width in global memory ([n][l])
+    const int SR = RL * NP + 4;        // staged row stride ([l][n_padded])
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -63,6 +68,9 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     T* Rs = reinterpret_cast<T*>(base + align16(size_t(32) * SY * sizeof(T)));
     T* Cs = reinterpret_cast<T*>(base + align16(size_t(32) * SY * sizeof(T)) + align16(size_t(32) * SR * sizeof(T)));
     const int nout = nr * K;
+    // zero the padding channels once (never overwritten)
+    for (int t = lane; t < 32 * SR; t += 32) Rs[t] = T(0);
+    __syncwarp();
 
     for (int64_t i = int64_t(blockIdx.x) * W + warp; i < ncent; i += int64_t(gridDim.x) * W) {
         const int64_t e0 = offsets[i], e1 = offsets[i + 1];
@@ -87,12 +95,15 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                 ValVis<T, K> vis{Ys + size_t(lane) * SY};
                 point_core<L, false, false>(x, y, z, r2, tb, vis);
             }
-            {  // this chunk's radial rows, coalesced, into odd-stride rows
+            {  // this chunk's radial rows: coalesced reads, [n][l] -> [l][n] in shared memory
                 const T* src = R + ch * RW;
                 const int total = cnt * RW;
                 for (int t = lane; t < total; t += 32) {
                     const int r = t / RW;
-                    Rs[r * SR + (t - r * RW)] = src[t];
+                    const int q = t - r * RW;
+                    const int n = q / RL;
+                    const int l = q - n * RL;
+                    Rs[r * SR + l * NP + n] = src[t];
                 }
             }
             __syncwarp();
@@ -102,12 +113,19 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                     T acc[kExpansionAcc];
 #pragma unroll
                     for (int b = 0; b < kExpansionAcc; ++b) acc[b] = (n0 + b < nr) ? Cs[(n0 + b) * K + k] : T(0);
+                    const T* rcol = Rs + l * NP + n0;
+#pragma unroll 4
                     for (int e = 0; e < cnt; ++e) {
                         const T yv = Ys[e * SY + k];
-                        const T* re = Rs + e * SR + l;
+                        const T* re = rcol + e * SR;
+                        if (n0 + kExpansionAcc <= NP) {
 #pragma unroll
-                        for (int b = 0; b < kExpansionAcc; ++b)
-                            if (n0 + b < nr) acc[b] += re[(n0 + b) * RL] * yv;
+                            for (int b = 0; b < kExpansionAcc; ++b) acc[b] += re[b] * yv;
+                        } else {
+#pragma unroll
+                            for (int b = 0; b < kExpansionAcc; ++b)
+                                if (n0 + b < NP) acc[b] += re[b] * yv;
+                        }
                     }
 #pragma unroll
                     for (int b = 0; b < kExpansionAcc; ++b)
@@ -221,7 +239,8 @@ extern "C" int sphericart_expansion(const void* xyz, const void* radial, const i
               status};
     // Fit the per-warp staging (Y rows, R rows, accumulators) in the opt-in limit.
     const size_t K = size_t(l_max + 1) * (l_max + 1);
-    const size_t per_warp = e * (32 * (K + 1) + 32 * (size_t(n_rad) * (l_max + 1) + 1) + size_t(n_rad) * K) + 48;
+    const size_t per_warp =
+        e * (32 * (K + 1) + 32 * (size_t((n_rad + 3) / 4 * 4) * (l_max + 1) + 4) + size_t(n_rad) * K) + 48;
     while (a.warps > 1 && size_t(a.warps) * per_warp > size_t(max_smem_optin())) --a.warps;
     if (per_warp > size_t(max_smem_optin())) {
         set_error("expansion: n_rad=%d with l_max=%d needs %zu bytes of shared memory per warp", n_rad, l_max,
