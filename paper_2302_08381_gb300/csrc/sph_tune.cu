@@ -76,7 +76,7 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, i
     sph_launch best_s{0, 0, 0, 0};
     const int Ps[] = {32, 28, 24, 20, 16, 12, 8, 4, 2, 1};
     const int Ws[] = {1, 2, 4, 8};
-    const int Bs[] = {0, 1, 2, 3, 4, 6, 8};
+    const int Bs[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};  // > occupancy: blocks scheduled in waves
     for (int P : Ps) {
         if (P % mult != 0) continue;
         for (int W : Ws) {
@@ -136,7 +136,7 @@ int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream
     // points_per_tile here scales the per-warp budget (in l_max = 8 gradient rows).
     const int budgets[] = {32, 24, 16, 12, 8};
     const int Ws[] = {1, 2, 4};
-    const int Bs[] = {0, 2, 3, 4};
+    const int Bs[] = {0, 2, 3, 4, 8, 16};
     for (int bud : budgets)
         for (int W : Ws)
             for (int B : Bs) {
