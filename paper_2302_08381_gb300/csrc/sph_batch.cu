@@ -58,7 +58,8 @@ struct BatchVis {
 
 template <int L>
 __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigned char* buf,
-                                           const PointTabs<16, float, false>& tb, int lane) {
+                                           const PointTabs<16, float, false>& tb, int lane, float px, float py,
+                                           float pz) {
     constexpr int K = (L + 1) * (L + 1);
     using RS = RowStride<L>;
     const int P = s.P;
@@ -71,7 +72,13 @@ __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigne
     // rows j, j+32, ... so that every set's tile fills the per-warp budget.
     for (int row = lane; row < cnt; row += 32) {
         const int64_t p = p0 + row;
-        float x = s.xyz[3 * p], y = s.xyz[3 * p + 1], z = s.xyz[3 * p + 2];
+        // the first row's coordinates were prefetched by the caller
+        float x = px, y = py, z = pz;
+        if (row != lane) {
+            x = s.xyz[3 * p];
+            y = s.xyz[3 * p + 1];
+            z = s.xyz[3 * p + 2];
+        }
         float r2, ir = 1.f;
         if (s.norm) {
             unit_point(x, y, z, r2, ir);
@@ -115,6 +122,8 @@ struct BatchTabs {
     PointTabs<16, float, false> t;
 };
 
+constexpr int kBatchRun = 4;  // consecutive tiles a warp takes per counter increment
+
 __global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__ sets, int nsets,
                                                     int64_t total_tiles, unsigned long long* __restrict__ counter,
                                                     int per_warp_bytes, const __grid_constant__ BatchTabs tabs) {
@@ -122,29 +131,58 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* buf = smem + size_t(warp) * per_warp_bytes;
-    // The next tile index is fetched one tile ahead, so the atomic's round
-    // trip overlaps the current tile's work.
-    unsigned long long nxt = 0;
-    if (lane == 0) nxt = atomicAdd(counter, 1ull);
-    for (;;) {
-        const unsigned long long t = __shfl_sync(0xffffffffu, nxt, 0);
-        if (t >= static_cast<unsigned long long>(total_tiles)) break;
-        if (lane == 0) nxt = atomicAdd(counter, 1ull);
-        // Binary search for the set holding tile t.
-        int lo = 0, hi = nsets - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sets[mid].tile_begin <= int64_t(t))
-                lo = mid;
-            else
-                hi = mid - 1;
+    // Warps take runs of kBatchRun consecutive tiles from the counter (the
+    // next run is requested one run ahead). Runs are handed out in increasing
+    // order, so each warp finds a tile's set by scanning forward from the set
+    // of its previous tile, and prefetches the next tile's coordinates while
+    // the current tile is computed.
+    unsigned long long run = 0, nrun = 0;
+    if (lane == 0) run = atomicAdd(counter, 1ull);
+    run = __shfl_sync(0xffffffffu, run, 0);
+    if (lane == 0) nrun = atomicAdd(counter, 1ull);
+    int si = 0;
+    BatchSet s = sets[0];
+    int64_t s_end = (nsets > 1) ? sets[1].tile_begin : total_tiles;
+    auto locate = [&](int64_t t) {  // forward scan: t never decreases for a warp
+        while (t >= s_end && si + 1 < nsets) {
+            ++si;
+            s = sets[si];
+            s_end = (si + 1 < nsets) ? sets[si + 1].tile_begin : total_tiles;
         }
-        const BatchSet s = sets[lo];
-        const int64_t lt = int64_t(t) - s.tile_begin;
-        switch (s.L) {
+    };
+    auto prefetch = [&](int64_t t, float& x, float& y, float& z) {
+        const int64_t p = (t - s.tile_begin) * s.P + lane;
+        if (lane < s.P && p < s.n) {
+            x = s.xyz[3 * p];
+            y = s.xyz[3 * p + 1];
+            z = s.xyz[3 * p + 2];
+        }
+    };
+    int64_t t = int64_t(run) * kBatchRun;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (t < total_tiles) {
+        locate(t);
+        prefetch(t, px, py, pz);
+    }
+    while (t < total_tiles) {
+        // next tile: the following one in this run, else the first of the next run
+        int64_t tn = t + 1;
+        if (tn % kBatchRun == 0) {
+            const unsigned long long r = __shfl_sync(0xffffffffu, nrun, 0);
+            tn = int64_t(r) * kBatchRun;
+            if (lane == 0) nrun = atomicAdd(counter, 1ull);
+        }
+        const BatchSet cur = s;
+        const int64_t lt = t - cur.tile_begin;
+        const float cx = px, cy = py, cz = pz;
+        if (tn < total_tiles) {
+            locate(tn);
+            prefetch(tn, px, py, pz);
+        }
+        switch (cur.L) {
 #define SPH_CASE(LL) \
     case LL:         \
-        batch_tile<LL>(s, lt, buf, tabs.t, lane); \
+        batch_tile<LL>(cur, lt, buf, tabs.t, lane, cx, cy, cz); \
         break;
             SPH_CASE(0) SPH_CASE(1) SPH_CASE(2) SPH_CASE(3) SPH_CASE(4) SPH_CASE(5) SPH_CASE(6) SPH_CASE(7)
             SPH_CASE(8) SPH_CASE(9) SPH_CASE(10) SPH_CASE(11) SPH_CASE(12) SPH_CASE(13) SPH_CASE(14)
@@ -153,6 +191,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__
             default:
                 break;
         }
+        t = tn;
     }
     if (lane == 0) bulk_wait_all();
 }
