@@ -195,13 +195,15 @@ def recorded_traffic(kernel_tag: str):
     ent = rec.get(kernel_tag)
     if not ent:
         return None
+    # hash of the files that define the kernel (listed in the record)
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2302_08381_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
-    if ent.get("sources_sha256") != h.hexdigest():
+    for rel in ent.get("source_files", []):
+        path = os.path.join(ROOT, rel)
+        if not os.path.exists(path):
+            return None
+        with open(path, "rb") as f:
+            h.update(rel.encode() + f.read())
+    if not ent.get("source_files") or ent.get("sources_sha256") != h.hexdigest():
         return None
     return ent.get("bytes_per_launch")
 
