@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "bwd", "dbwd", "batch"],
+        choices=["fwd", "bwd", "dbwd", "batch", "expansion"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     args = ap.parse_args()
@@ -448,7 +448,7 @@ def run_profile(args):
     if args.profile in ("fwd", "batch"):
         L = L_MAX
     else:
-        L = BWD_L
+        L = BWD_L  # backward kernels and the expansion: l_max = 6
     K = (L + 1) ** 2
     x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).to(dev)
     if args.profile == "fwd":
@@ -463,6 +463,15 @@ def run_profile(args):
             fn = lambda: api.backward(x, g, L, out=dx)  # noqa: E731
         else:
             fn = lambda: api.double_backward(x, g, v, L)  # noqa: E731
+    elif args.profile == "expansion":
+        nr, ncent = 8, max(1, n // 40)
+        counts = np.full(ncent, n // ncent, dtype=np.int64)
+        offs = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)).to(dev)
+        E = int(counts.sum())
+        R = torch.from_numpy(inputs.upstream(E, nr * (L + 1), seed=612)).to(dev).view(E, nr, L + 1)
+        xe = x[:E].contiguous()
+        c = torch.empty((ncent, nr, K), device=dev)
+        fn = lambda: api.expansion(xe, R, offs, L, out=c)  # noqa: E731
     else:
         sizes, lmax, xyz = inputs.ragged_sets(512, [3, 6, 8, 12], 1000, 200_000, seed=5)
         scale = n / float(sizes.sum())

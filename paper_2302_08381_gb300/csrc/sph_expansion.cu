@@ -97,13 +97,11 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             }
             {  // this chunk's radial rows: coalesced reads, [n][l] -> [l][n] in shared memory
                 const T* src = R + ch * RW;
-                const int total = cnt * RW;
-                for (int t = lane; t < total; t += 32) {
-                    const int r = t / RW;
-                    const int q = t - r * RW;
-                    const int n = q / RL;
-                    const int l = q - n * RL;
-                    Rs[r * SR + l * NP + n] = src[t];
+                for (int r = 0; r < cnt; ++r) {
+                    for (int q = lane; q < RW; q += 32) {
+                        const int n = q / RL;  // RL is a compile-time constant
+                        Rs[r * SR + (q - n * RL) * NP + n] = src[r * RW + q];
+                    }
                 }
             }
             __syncwarp();
