@@ -33,18 +33,38 @@ __device__ __forceinline__ int l_of_column(int k) {
     return l;
 }
 
-// Radial channels per point are staged as [l][n] with n padded to a multiple
-// of 4 (zeros), so the kExpansionAcc factors a column needs are contiguous
-// and 16-byte aligned.
-__host__ __device__ constexpr int padded_rad(int nr) { return (nr + 3) / 4 * 4; }
-
+// Per-warp shared memory: Y rows of a 32-point chunk (odd stride), two
+// buffers of the chunk's radial rows in their global layout [e][n][l]
+// (filled by bulk copies one chunk ahead), the [n_rad, K] accumulator of the
+// current centre, and two mbarriers.
 template <int L, typename T>
 __host__ __device__ constexpr size_t expansion_warp_bytes(int nr) {
     constexpr int K = (L + 1) * (L + 1);
     constexpr int SY = (K % 2 == 0) ? K + 1 : K;
-    const int SR = (L + 1) * padded_rad(nr) + 4;  // row stride, a multiple of 4 (16-byte rows)
-    return align16(size_t(32) * SY * sizeof(T)) + align16(size_t(32) * SR * sizeof(T)) +
-           align16(size_t(nr) * K * sizeof(T));
+    const int RW = nr * (L + 1);
+    return align16(size_t(32) * SY * sizeof(T)) + 2 * align16(size_t(32) * RW * sizeof(T)) +
+           align16(size_t(nr) * K * sizeof(T)) + 16;
+}
+
+// The work of one warp is the sequence of (centre, 32-point chunk) items of
+// the centres i = first, first + stride, ...; `next_item` advances along it.
+struct ExpItem {
+    int64_t i;   // centre (>= ncent: done)
+    int64_t ch;  // first point of the chunk
+    int64_t e1;  // end of the centre's points
+    bool valid_centre;
+};
+
+__device__ __forceinline__ void first_chunk(ExpItem& it, const int64_t* __restrict__ offsets, int64_t ncent,
+                                            int64_t npts, int64_t stride) {
+    while (it.i < ncent) {
+        const int64_t e0 = offsets[it.i], e1 = offsets[it.i + 1];
+        it.valid_centre = !(e0 < 0 || e1 < e0 || e1 > npts);
+        it.ch = e0;
+        it.e1 = e1;
+        return;  // empty and malformed centres are items too (they write their output)
+    }
+    (void)stride;
 }
 
 template <int L, bool NORM, typename T>
@@ -52,89 +72,171 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                                                         const int64_t* __restrict__ offsets, int64_t ncent,
                                                         int64_t npts, int nr,
                                                         const __grid_constant__ PointTabs<L, T, false> tb,
-                                                        T* __restrict__ c, uint32_t* __restrict__ status) {
+                                                        T* __restrict__ c, uint32_t* __restrict__ status, int bulk) {
     constexpr int K = (L + 1) * (L + 1);
     constexpr int SY = (K % 2 == 0) ? K + 1 : K;
     constexpr int RL = L + 1;
-    const int NP = padded_rad(nr);
-    const int RW = nr * RL;            // R row width in global memory ([n][l])
-    const int SR = RL * NP + 4;        // staged row stride ([l][n_padded])
+    const int RW = nr * RL;  // radial row width ([n][l])
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
     unsigned char* base = smem + size_t(warp) * expansion_warp_bytes<L, T>(nr);
+    const size_t ybytes = align16(size_t(32) * SY * sizeof(T));
+    const size_t rbytes = align16(size_t(32) * RW * sizeof(T));
     T* Ys = reinterpret_cast<T*>(base);
-    T* Rs = reinterpret_cast<T*>(base + align16(size_t(32) * SY * sizeof(T)));
-    T* Cs = reinterpret_cast<T*>(base + align16(size_t(32) * SY * sizeof(T)) + align16(size_t(32) * SR * sizeof(T)));
+    T* Rb0 = reinterpret_cast<T*>(base + ybytes);
+    T* Rb1 = reinterpret_cast<T*>(base + ybytes + rbytes);
+    T* Cs = reinterpret_cast<T*>(base + ybytes + 2 * rbytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + 2 * rbytes + align16(size_t(nr) * K * sizeof(T)));
     const int nout = nr * K;
-    // zero the padding channels once (never overwritten)
-    for (int t = lane; t < 32 * SR; t += 32) Rs[t] = T(0);
-    __syncwarp();
+    const int64_t stride = int64_t(gridDim.x) * W;
 
-    for (int64_t i = int64_t(blockIdx.x) * W + warp; i < ncent; i += int64_t(gridDim.x) * W) {
-        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        T* ci = c + i * nout;
-        if (e0 < 0 || e1 < e0 || e1 > npts) {  // malformed CSR: flag it, write zeros
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    uint32_t phase = 0, pending = 0;
+    bool failed = false;
+
+    // Issues the radial rows of chunk (ch, cnt) into buffer b: bulk copy of
+    // the whole rows when allowed, else nothing (loaded at use time).
+    auto issue = [&](int b, int64_t ch, int cnt) -> int64_t {
+        if (!bulk || cnt <= 0) return 0;
+        const uint32_t bytes = uint32_t(size_t(cnt) * RW * sizeof(T));
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bar[b], bytes);
+            bulk_load(b ? Rb1 : Rb0, R + ch * RW, bytes, &bar[b]);
+        }
+        pending |= (1u << b);
+        return cnt;
+    };
+
+    ExpItem cur{int64_t(blockIdx.x) * W + warp, 0, 0, true};
+    first_chunk(cur, offsets, ncent, npts, stride);
+    int b = 0;
+    if (cur.i < ncent && cur.valid_centre) issue(0, cur.ch, int(min(int64_t(32), cur.e1 - cur.ch)));
+    T px = T(0), py = T(0), pz = T(0);  // this lane's coordinates for the current chunk
+    if (cur.i < ncent && cur.valid_centre && cur.ch + lane < cur.e1) {
+        const int64_t p = cur.ch + lane;
+        px = xyz[3 * p];
+        py = xyz[3 * p + 1];
+        pz = xyz[3 * p + 2];
+    }
+    bool new_centre = true;
+    while (cur.i < ncent) {
+        T* ci = c + cur.i * nout;
+        if (!cur.valid_centre) {  // malformed CSR: flag it, write zeros, move on
             if (lane == 0) atomicOr(status, kStatusBadOffsets);
             for (int o = lane; o < nout; o += 32) ci[o] = T(0);
+            cur.i += stride;
+            first_chunk(cur, offsets, ncent, npts, stride);
+            if (cur.i < ncent && cur.valid_centre) {
+                issue(b, cur.ch, int(min(int64_t(32), cur.e1 - cur.ch)));
+                if (cur.ch + lane < cur.e1) {
+                    const int64_t p = cur.ch + lane;
+                    px = xyz[3 * p];
+                    py = xyz[3 * p + 1];
+                    pz = xyz[3 * p + 2];
+                }
+            }
+            new_centre = true;
             continue;
         }
-        for (int o = lane; o < nout; o += 32) Cs[o] = T(0);
-        for (int64_t ch = e0; ch < e1; ch += 32) {
-            const int cnt = int(min(int64_t(32), e1 - ch));
-            if (lane < cnt) {
-                const int64_t p = ch + lane;
-                T x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
-                T r2, ir = T(1);
-                if (NORM) {
-                    unit_point(x, y, z, r2, ir);
-                } else {
-                    r2 = x * x + y * y + z * z;
-                }
-                ValVis<T, K> vis{Ys + size_t(lane) * SY};
-                point_core<L, false, false>(x, y, z, r2, tb, vis);
-            }
-            {  // this chunk's radial rows: coalesced reads, [n][l] -> [l][n] in shared memory
-                const T* src = R + ch * RW;
-                for (int r = 0; r < cnt; ++r) {
-                    for (int q = lane; q < RW; q += 32) {
-                        const int n = q / RL;  // RL is a compile-time constant
-                        Rs[r * SR + (q - n * RL) * NP + n] = src[r * RW + q];
-                    }
-                }
-            }
-            __syncwarp();
-            for (int k = lane; k < K; k += 32) {
-                const int l = l_of_column(k);
-                for (int n0 = 0; n0 < nr; n0 += kExpansionAcc) {
-                    T acc[kExpansionAcc];
-#pragma unroll
-                    for (int b = 0; b < kExpansionAcc; ++b) acc[b] = (n0 + b < nr) ? Cs[(n0 + b) * K + k] : T(0);
-                    const T* rcol = Rs + l * NP + n0;
-#pragma unroll 4
-                    for (int e = 0; e < cnt; ++e) {
-                        const T yv = Ys[e * SY + k];
-                        const T* re = rcol + e * SR;
-                        if (n0 + kExpansionAcc <= NP) {
-#pragma unroll
-                            for (int b = 0; b < kExpansionAcc; ++b) acc[b] += re[b] * yv;
-                        } else {
-#pragma unroll
-                            for (int b = 0; b < kExpansionAcc; ++b)
-                                if (n0 + b < NP) acc[b] += re[b] * yv;
-                        }
-                    }
-#pragma unroll
-                    for (int b = 0; b < kExpansionAcc; ++b)
-                        if (n0 + b < nr) Cs[(n0 + b) * K + k] = acc[b];
-                }
-            }
-            __syncwarp();
+        if (new_centre) {
+            for (int o = lane; o < nout; o += 32) Cs[o] = T(0);
+            new_centre = false;
         }
-        for (int o = lane; o < nout; o += 32) ci[o] = Cs[o];
+        const int cnt = int(min(int64_t(32), cur.e1 - cur.ch));
+        // the next item: the centre's next chunk, else the next centre's first
+        ExpItem nx = cur;
+        nx.ch = cur.ch + 32;
+        bool nx_new_centre = false;
+        if (nx.ch >= cur.e1) {
+            nx.i = cur.i + stride;
+            first_chunk(nx, offsets, ncent, npts, stride);
+            nx_new_centre = true;
+        }
+        const int nb = b ^ 1;
+        T nxx = T(0), nxy = T(0), nxz = T(0);
+        if (nx.i < ncent && nx.valid_centre && !failed) {
+            issue(nb, nx.ch, int(min(int64_t(32), nx.e1 - nx.ch)));
+            if (nx.ch + lane < nx.e1) {
+                const int64_t p = nx.ch + lane;
+                nxx = xyz[3 * p];
+                nxy = xyz[3 * p + 1];
+                nxz = xyz[3 * p + 2];
+            }
+        }
+        // harmonics of this chunk, one point per lane
+        if (lane < cnt) {
+            T x = px, y = py, z = pz, r2, ir = T(1);
+            if (NORM) {
+                unit_point(x, y, z, r2, ir);
+            } else {
+                r2 = x * x + y * y + z * z;
+            }
+            ValVis<T, K> vis{Ys + size_t(lane) * SY};
+            point_core<L, false, false>(x, y, z, r2, tb, vis);
+        }
+        T* const Rs = b ? Rb1 : Rb0;
+        if (pending & (1u << b)) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, kWaitPolls);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (ok) {
+                phase ^= (1u << b);
+                pending &= ~(1u << b);
+            } else {
+                if (lane == 0) atomicOr(status, kStatusLoadTimeout);
+                failed = true;
+                break;
+            }
+        } else {
+            const T* src = R + cur.ch * RW;
+            for (int t = lane; t < cnt * RW; t += 32) Rs[t] = src[t];
+        }
         __syncwarp();
+        for (int k = lane; k < K; k += 32) {
+            const int l = l_of_column(k);
+            for (int n0 = 0; n0 < nr; n0 += kExpansionAcc) {
+                T acc[kExpansionAcc];
+#pragma unroll
+                for (int q = 0; q < kExpansionAcc; ++q) acc[q] = (n0 + q < nr) ? Cs[(n0 + q) * K + k] : T(0);
+                const T* rcol = Rs + n0 * RL + l;
+#pragma unroll 4
+                for (int e = 0; e < cnt; ++e) {
+                    const T yv = Ys[e * SY + k];
+                    const T* re = rcol + e * RW;
+#pragma unroll
+                    for (int q = 0; q < kExpansionAcc; ++q)
+                        if (n0 + q < nr) acc[q] += re[q * RL] * yv;
+                }
+#pragma unroll
+                for (int q = 0; q < kExpansionAcc; ++q)
+                    if (n0 + q < nr) Cs[(n0 + q) * K + k] = acc[q];
+            }
+        }
+        fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
+        __syncwarp();
+        if (nx_new_centre) {  // centre finished: write it out
+            for (int o = lane; o < nout; o += 32) ci[o] = Cs[o];
+            __syncwarp();
+            new_centre = true;
+        }
+        cur = nx;
+        b = nb;
+        px = nxx;
+        py = nxy;
+        pz = nxz;
     }
+    if (pending && lane == 0) {  // after a timeout: bounded wait for copies still in flight
+        for (int q = 0; q < 2; ++q)
+            if (pending & (1u << q)) (void)mbar_wait_bounded(&bar[q], (phase >> q) & 1u, kWaitPolls);
+    }
+    __syncwarp();
 }
 
 struct ExpArgs {
@@ -162,9 +264,12 @@ int launch_expansion(const ExpArgs& a) {
     cudaError_t err = ensure_smem(kern, smem);
     if (err != cudaSuccess) return int(err);
     const int grid = grid_for(kern, 32 * W, smem, a.ncent, 0);
+    // Bulk copies of whole chunks need 16-byte aligned rows of the radial array.
+    const bool bulk = (reinterpret_cast<uintptr_t>(a.radial) % 16 == 0) &&
+                      ((size_t(a.nr) * (L + 1) * sizeof(T)) % 16 == 0);
     kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
         static_cast<const T*>(a.xyz), static_cast<const T*>(a.radial), a.offsets, a.ncent, a.npts, a.nr, tb,
-        static_cast<T*>(a.c), a.status);
+        static_cast<T*>(a.c), a.status, bulk ? 1 : 0);
     return int(cudaGetLastError());
 }
 
@@ -237,8 +342,7 @@ extern "C" int sphericart_expansion(const void* xyz, const void* radial, const i
               status};
     // Fit the per-warp staging (Y rows, R rows, accumulators) in the opt-in limit.
     const size_t K = size_t(l_max + 1) * (l_max + 1);
-    const size_t per_warp =
-        e * (32 * (K + 1) + 32 * (size_t((n_rad + 3) / 4 * 4) * (l_max + 1) + 4) + size_t(n_rad) * K) + 48;
+    const size_t per_warp = e * (32 * (K + 1) + 2 * 32 * size_t(n_rad) * (l_max + 1) + size_t(n_rad) * K) + 80;
     while (a.warps > 1 && size_t(a.warps) * per_warp > size_t(max_smem_optin())) --a.warps;
     if (per_warp > size_t(max_smem_optin())) {
         set_error("expansion: n_rad=%d with l_max=%d needs %zu bytes of shared memory per warp", n_rad, l_max,
