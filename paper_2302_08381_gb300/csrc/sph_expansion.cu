@@ -18,20 +18,12 @@ namespace sph {
 
 constexpr uint32_t kStatusBadOffsets = 2u;
 constexpr int kExpansionMaxRad = 64;
-constexpr int kExpansionAcc = 8;  // radial channels accumulated per register pass
 
 template <typename T, int K>
 struct ValVis {
     T* row;
     __device__ __forceinline__ void emit(int, int k, const Deriv<T>& d) { row[k] = d.v; }
 };
-
-__device__ __forceinline__ int l_of_column(int k) {
-    int l = int(sqrtf(float(k)));
-    if ((l + 1) * (l + 1) <= k) ++l;
-    if (l * l > k) --l;
-    return l;
-}
 
 // Per-warp shared memory: Y rows of a 32-point chunk (odd stride), two
 // buffers of the chunk's radial rows in their global layout [e][n][l]
@@ -91,6 +83,11 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + 2 * rbytes + align16(size_t(nr) * K * sizeof(T)));
     const int nout = nr * K;
     const int64_t stride = int64_t(gridDim.x) * W;
+    const int NG = (nr + 3) / 4;  // radial channel groups of 4
+    int col_groups = 0;           // sum over l of ceil((2l+1)/4)
+#pragma unroll
+    for (int ll = 0; ll <= L; ++ll) col_groups += (2 * ll + 1 + 3) / 4;
+    const int n_items = col_groups * NG;
 
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -199,25 +196,55 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             for (int t = lane; t < cnt * RW; t += 32) Rs[t] = src[t];
         }
         __syncwarp();
-        for (int k = lane; k < K; k += 32) {
-            const int l = l_of_column(k);
-            for (int n0 = 0; n0 < nr; n0 += kExpansionAcc) {
-                T acc[kExpansionAcc];
-#pragma unroll
-                for (int q = 0; q < kExpansionAcc; ++q) acc[q] = (n0 + q < nr) ? Cs[(n0 + q) * K + k] : T(0);
-                const T* rcol = Rs + n0 * RL + l;
-#pragma unroll 4
-                for (int e = 0; e < cnt; ++e) {
-                    const T yv = Ys[e * SY + k];
-                    const T* re = rcol + e * RW;
-#pragma unroll
-                    for (int q = 0; q < kExpansionAcc; ++q)
-                        if (n0 + q < nr) acc[q] += re[q * RL] * yv;
+        // Contraction, register-blocked: a work item is up to 4 columns of one
+        // l block x 4 radial channels (16 accumulators); items are ordered by
+        // (l, column group, channel group) and dealt to lanes round-robin.
+        // Out-of-range columns/channels of an item read a valid entry and are
+        // masked at the write-back, so the inner loop has no predicates.
+        for (int it = lane; it < n_items; it += 32) {
+            int l = 0, acc_items = 0;
+            for (int ll = 0; ll <= L; ++ll) {  // decode the item
+                const int cnt_l = ((2 * ll + 1 + 3) / 4) * NG;
+                if (it < acc_items + cnt_l) {
+                    l = ll;
+                    break;
                 }
-#pragma unroll
-                for (int q = 0; q < kExpansionAcc; ++q)
-                    if (n0 + q < nr) Cs[(n0 + q) * K + k] = acc[q];
+                acc_items += cnt_l;
             }
+            const int r = it - acc_items;
+            const int cg = r / NG;
+            const int n0 = (r - cg * NG) * 4;
+            const int c0 = l * l + cg * 4;
+            const int nc = min(4, 2 * l + 1 - cg * 4);
+            int col[4], rof[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) col[j] = c0 + min(j, nc - 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rof[q] = min(n0 + q, nr - 1) * RL + l;
+            T acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[j][q] = Cs[min(n0 + q, nr - 1) * K + col[j]];
+#pragma unroll 2
+            for (int e = 0; e < cnt; ++e) {
+                const T* ye = Ys + e * SY;
+                const T* re = Rs + e * RW;
+                T yv[4], rv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) yv[j] = ye[col[j]];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) rv[q] = re[rof[q]];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[j][q] += yv[j] * rv[q];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j < nc && n0 + q < nr) Cs[(n0 + q) * K + col[j]] = acc[j][q];
         }
         fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
         __syncwarp();
