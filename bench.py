@@ -589,6 +589,12 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (100_000, 8, "l8_values_f32_n100k", dict(), 4, 1),
         (100_000, 8, "l8_grad_f32_n100k", dict(gradients=True), 4, 4),
         (100_000, 8, "l8_grad_f64_n100k", dict(gradients=True), 8, 4),
+        # the high-degree precision-sweep sizes (SLICE kernels), normalized
+        (200_000, 20, "l20_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
+        (200_000, 30, "l30_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
+        (200_000, 50, "l50_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
+        (200_000, 50, "l50_grad_mixed_norm_n200k", dict(gradients=True, normalized=True, qprec="f64"), 4, 4),
+        (200_000, 50, "l50_grad_f64_norm_n200k", dict(gradients=True, normalized=True), 8, 4),
     ):
         dt = torch.float64 if elem == 8 else torch.float32
         x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)

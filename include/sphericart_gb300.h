@@ -295,8 +295,8 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized,
 /* sphericart_batch_autotune: times batch plans for these sets over a grid of
  * per-warp shared-memory budgets, warps per block and blocks per SM, and
  * returns the fastest shape for sphericart_batch_plan_create (for batch plans
- * points_per_tile sets the per-warp budget as that many l_max = 8 FP32
- * value+gradient rows of 1296 bytes).
+ * points_per_tile, 0..160, sets the per-warp budget as that many l_max = 8
+ * FP32 value+gradient rows of 1296 bytes; 0 = 32 rows).
  * Overwrites the sets' outputs; synchronises. */
 int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream,
                               int reps, sph_launch* best, float* best_ms);

@@ -262,8 +262,8 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
     }
     sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
     const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
-    if (W > 8) {
-        set_error("warps_per_block=%d must be in [1,8]", W);
+    if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 160) {
+        set_error("warps_per_block=%d must be in [1,8], points_per_tile (budget rows) in [0,160]", W);
         return SPH_EINVAL;
     }
     // Per-warp shared-memory budget: one 32-point l_max = 8 value+gradient tile.
@@ -450,7 +450,7 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
     }
     const sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
     const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
-    if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 32 || lau.blocks_per_sm < 0) {
+    if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 160 || lau.blocks_per_sm < 0) {
         set_error("batch_compute_noalloc: bad launch shape");
         return SPH_EINVAL;
     }

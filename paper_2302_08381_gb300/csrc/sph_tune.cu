@@ -134,7 +134,7 @@ int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream
     float best_t = 1e30f;
     sph_launch best_s{0, 0, 0, 0};
     // points_per_tile here scales the per-warp budget (in l_max = 8 gradient rows).
-    const int budgets[] = {32, 24, 16, 12, 8};
+    const int budgets[] = {64, 48, 32, 24, 16, 12, 8};
     const int Ws[] = {1, 2, 4};
     const int Bs[] = {0, 2, 3, 4, 8, 16};
     for (int bud : budgets)
