@@ -579,7 +579,8 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (4_194_304, 8, "l8_grad_f32_normalized", dict(normalized=True, gradients=True), 4, 4),
         (4_194_304, 8, "l8_grad_bf16_store", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
         (4_194_304, 8, "l8_grad_f64", dict(gradients=True), 8, 4),
-        (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True), 4, 13),
+        (1_048_576, 8, "l8_grad_hess_f32", dict(gradients=True, hessians=True), 4, 13),
+        (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True, kernel="slice"), 4, 13),
         (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
         (1_000_000, 10, "l10_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
         # the paper's GPU table sizes (10k / 100k points, l_max = 8)

@@ -76,8 +76,8 @@ typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
  * the c_m/s_m powers, not from the Q recursion alone. SLICE kernels only. */
 typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
-/* Kernel family. AUTO picks POINT when l_max <= SPH_MAX_L_POINT and no Hessian
- * is requested, else SLICE.
+/* Kernel family. AUTO picks POINT when l_max <= SPH_MAX_L_POINT (except for
+ * the mixed precision mode and bfloat16 Hessians), else SLICE.
  *   POINT: one thread per point, the whole (l, m) recursion unrolled in
  *          registers for a compile-time l_max, outputs staged in shared memory
  *          and written with bulk (TMA) copies.
@@ -115,8 +115,8 @@ int sphericart_compute(const float* xyz, int64_t n, int l_max, int normalized,
  *   dtype  sph_dtype of xyz and of the arithmetic
  *   out    sph_out storage of sph/dsph/ddsph (element size 4, 8 or 2 bytes)
  *   qprec  sph_qprec of the Q recursion (SPH_Q_F64 with SPH_F32 only)
- *   kernel sph_kernel family; POINT with l_max > SPH_MAX_L_POINT or with
- *          ddsph returns SPH_EUNSUPPORTED
+ *   kernel sph_kernel family; POINT with l_max > SPH_MAX_L_POINT, with the
+ *          mixed mode or with bfloat16 Hessians returns SPH_EUNSUPPORTED
  *   launch NULL or a launch shape (zeros = default)
  * SPH_EUNSUPPORTED also for BF16 output with FP64 arithmetic. */
 int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
@@ -275,7 +275,8 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess,
 
 /* sphericart_set_launch: installs a tuned launch shape for forward calls with
  * this (l_max, dtype, out, grad) on the current device; used by AUTO/POINT
- * calls that pass launch == NULL. points_per_tile etc. are validated. */
+ * calls that pass launch == NULL (grad: 0 values, 1 + gradients, 2 + gradients
+ * and Hessians). points_per_tile etc. are validated. */
 int sphericart_set_launch(int l_max, int dtype, int out, int grad,
                           const sph_launch* launch);
 

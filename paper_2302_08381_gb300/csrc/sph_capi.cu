@@ -144,8 +144,8 @@ int tile_multiple(int L, int elem) {
     return 16 / gcd_int((K * elem) % 16 == 0 ? 16 : (K * elem) % 16, 16);
 }
 
-sph_launch default_point_fwd(int L, int grad, int elem) {
-    const size_t row = point_row_bytes(L, grad, elem);
+sph_launch default_point_fwd(int L, int grad, int elem, int hess = 0) {
+    const size_t row = point_row_bytes(L, grad, elem, hess);
     const int mult = tile_multiple(L, elem);
     const size_t budget = 48 * 1024;
     int P = 32;
@@ -212,7 +212,7 @@ bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s) {
         return false;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_tuned.find(TuneKey{d, L, dtype, out, grad ? 1 : 0});
+    auto it = g_tuned.find(TuneKey{d, L, dtype, out, grad >= 2 ? 2 : (grad ? 1 : 0)});
     if (it == g_tuned.end()) return false;
     *s = it->second;
     return true;
@@ -325,9 +325,11 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     const bool mixed = (dtype == SPH_F32 && qprec == SPH_Q_F64);
     const int grad = dsph ? 1 : 0;
     int fam = kernel;
-    if (fam == SPH_KERNEL_AUTO) fam = (l_max <= SPH_MAX_L_POINT && !ddsph && !mixed) ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE;
-    if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || ddsph || mixed)) {
-        set_error("POINT kernels take l_max <= %d, no Hessians and native Q precision", SPH_MAX_L_POINT);
+    const bool hess_bf16 = ddsph && out == SPH_OUT_BF16;
+    if (fam == SPH_KERNEL_AUTO)
+        fam = (l_max <= SPH_MAX_L_POINT && !hess_bf16 && !mixed) ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE;
+    if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || hess_bf16 || mixed)) {
+        set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
     if (n == 0) return SPH_OK;
@@ -352,11 +354,12 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             int d = -1;
             cudaGetDevice(&d);
             std::lock_guard<std::mutex> lk(g_mu);
-            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, grad});
+            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, ddsph ? 2 : grad});
             if (it != g_tuned.end()) a.launch = it->second;
         }
-        const sph_launch dflt = default_point_fwd(l_max, grad, eo);
-        if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo))) return SPH_EINVAL;
+        const int hess = ddsph ? 1 : 0;
+        const sph_launch dflt = default_point_fwd(l_max, grad, eo, hess);
+        if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo, hess))) return SPH_EINVAL;
         return cuda_status(point_fwd_fn(l_max)(a), "POINT forward launch");
     }
     if (!valid_lanes(a.launch)) return SPH_EINVAL;
@@ -453,7 +456,7 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         return SPH_EINVAL;
     }
     const int eo = elem_size(dtype, out);
-    if (l_max <= SPH_MAX_L_POINT && !hess) {
+    if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) {
         *kernel_out = SPH_KERNEL_POINT;
         sph_launch s{0, 0, 0, 0};
         int d = -1;
@@ -463,10 +466,10 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         }
         {
             std::lock_guard<std::mutex> lk(g_mu);
-            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, grad ? 1 : 0});
+            auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, hess ? 2 : (grad ? 1 : 0)});
             if (it != g_tuned.end()) s = it->second;
         }
-        const sph_launch dflt = default_point_fwd(l_max, grad ? 1 : 0, eo);
+        const sph_launch dflt = default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
         if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;
         if (s.warps_per_block == 0) s.warps_per_block = dflt.warps_per_block;
         *launch_out = s;
@@ -486,14 +489,15 @@ int sphericart_set_launch(int l_max, int dtype, int out, int grad, const sph_lau
     int st = ensure_device("set_launch");
     if (st) return st;
     const int eo = elem_size(dtype, out);
+    const int g = grad >= 2 ? 2 : (grad ? 1 : 0);  // 2: values + gradients + Hessians
     sph_launch s = *launch;
-    if (!resolve_point(s, default_point_fwd(l_max, grad ? 1 : 0, eo), l_max, eo,
-                       point_row_bytes(l_max, grad ? 1 : 0, eo)))
+    if (!resolve_point(s, default_point_fwd(l_max, g ? 1 : 0, eo, g == 2), l_max, eo,
+                       point_row_bytes(l_max, g ? 1 : 0, eo, g == 2)))
         return SPH_EINVAL;
     int d = -1;
     cudaGetDevice(&d);
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tuned[TuneKey{d, l_max, dtype, out, grad ? 1 : 0}] = s;
+    g_tuned[TuneKey{d, l_max, dtype, out, g}] = s;
     return SPH_OK;
 }
 

@@ -104,7 +104,7 @@ PointBwdFn point_dbwd_fn(int L);
 bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s);
 
 // Bytes of one output row of the POINT forward for this request.
-size_t point_row_bytes(int L, int grad, int elem);
+size_t point_row_bytes(int L, int grad, int elem, int hess = 0);
 
 // SLICE kernels (runtime l_max).
 int slice_fwd(const FwdArgs& a);

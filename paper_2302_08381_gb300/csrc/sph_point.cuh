@@ -137,17 +137,29 @@ __device__ __forceinline__ void point_core(T x, T y, T z, T r2, const Tabs& tb, 
 }
 
 // ------------------------------------------------------------------ forward
-template <typename T, typename TO, bool GRAD, bool NORM, int K>
+template <typename T, typename TO, bool GRAD, bool HESS, bool NORM, int K>
 struct FwdVis {
     TO* rv;  // this lane's sph row in shared memory
     TO* rd;  // this lane's dsph row (3 planes of K)
+    TO* rh;  // this lane's ddsph row (9 planes of K, i-major)
     T ux, uy, uz, ir;
     __device__ __forceinline__ void emit(int l, int k, Deriv<T> d) {
-        if (GRAD) {
-            if (NORM) normalize_deriv<false>(d, l, ux, uy, uz, ir);
+        if (GRAD || HESS) {
+            if (NORM) normalize_deriv<HESS>(d, l, ux, uy, uz, ir);
             rd[k] = OutConv<TO>::cv(d.gx);
             rd[K + k] = OutConv<TO>::cv(d.gy);
             rd[2 * K + k] = OutConv<TO>::cv(d.gz);
+        }
+        if (HESS) {
+            rh[0 * K + k] = OutConv<TO>::cv(d.hxx);
+            rh[1 * K + k] = OutConv<TO>::cv(d.hxy);
+            rh[2 * K + k] = OutConv<TO>::cv(d.hxz);
+            rh[3 * K + k] = OutConv<TO>::cv(d.hxy);
+            rh[4 * K + k] = OutConv<TO>::cv(d.hyy);
+            rh[5 * K + k] = OutConv<TO>::cv(d.hyz);
+            rh[6 * K + k] = OutConv<TO>::cv(d.hxz);
+            rh[7 * K + k] = OutConv<TO>::cv(d.hyz);
+            rh[8 * K + k] = OutConv<TO>::cv(d.hzz);
         }
         rv[k] = OutConv<TO>::cv(d.v);
     }
@@ -161,12 +173,14 @@ struct RowStride {
     static constexpr bool PAD = (K % 2 == 0);
     static constexpr int V = PAD ? K + 1 : K;          // sph / g rows
     static constexpr int D = PAD ? 3 * K + 1 : 3 * K;  // dsph rows
+    static constexpr int H = PAD ? 9 * K + 1 : 9 * K;  // ddsph rows
 };
 
-template <int L, bool GRAD, typename TO>
+template <int L, bool GRAD, bool HESS, typename TO>
 __host__ __device__ constexpr size_t point_fwd_warp_bytes(int P) {
     return align16(size_t(P) * RowStride<L>::V * sizeof(TO)) +
-           (GRAD ? align16(size_t(P) * RowStride<L>::D * sizeof(TO)) : 0);
+           (GRAD ? align16(size_t(P) * RowStride<L>::D * sizeof(TO)) : 0) +
+           (HESS ? align16(size_t(P) * RowStride<L>::H * sizeof(TO)) : 0);
 }
 
 // Copies `rows` rows of `cols` elements from a padded shared-memory image
@@ -192,11 +206,11 @@ __device__ __forceinline__ void warp_rows_in(T* __restrict__ sdst, const T* __re
     }
 }
 
-template <int L, bool GRAD, bool NORM, typename T, typename TO>
+template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO>
 __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xyz, int64_t n,
-                                                        const __grid_constant__ PointTabs<L, T, false> tb,
-                                                        TO* __restrict__ sph, TO* __restrict__ dsph, int P,
-                                                        int bulk) {
+                                                        const __grid_constant__ PointTabs<L, T, HESS> tb,
+                                                        TO* __restrict__ sph, TO* __restrict__ dsph,
+                                                        TO* __restrict__ ddsph, int P, int bulk) {
     constexpr int K = (L + 1) * (L + 1);
     using RS = RowStride<L>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -204,8 +218,10 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
     const size_t vbytes = align16(size_t(P) * RS::V * sizeof(TO));
-    TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point_fwd_warp_bytes<L, GRAD, TO>(P));
+    TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point_fwd_warp_bytes<L, GRAD, HESS, TO>(P));
     TO* s_d = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_v) + vbytes);
+    TO* s_h = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_d) +
+                                    (GRAD ? align16(size_t(P) * RS::D * sizeof(TO)) : 0));
 
     const int64_t ntiles = (n + P - 1) / P;
     const int64_t stride = int64_t(gridDim.x) * W;
@@ -242,26 +258,30 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
             } else {
                 r2 = x * x + y * y + z * z;
             }
-            FwdVis<T, TO, GRAD, NORM, K> vis{s_v + size_t(lane) * RS::V, s_d + size_t(lane) * RS::D, x, y, z, ir};
-            point_core<L, GRAD, false>(x, y, z, r2, tb, vis);
+            FwdVis<T, TO, GRAD, HESS, NORM, K> vis{s_v + size_t(lane) * RS::V, s_d + size_t(lane) * RS::D,
+                                                   s_h + size_t(lane) * RS::H, x, y, z, ir};
+            point_core<L, GRAD, HESS>(x, y, z, r2, tb, vis);
         }
         if constexpr (RS::PAD) {
             __syncwarp();
             warp_rows_out<K>(sph + p0 * K, s_v, cnt, RS::V, lane);
             if (GRAD) warp_rows_out<3 * K>(dsph + p0 * 3 * K, s_d, cnt, RS::D, lane);
+            if (HESS) warp_rows_out<9 * K>(ddsph + p0 * 9 * K, s_h, cnt, RS::H, lane);
             __syncwarp();
             continue;
         }
         fence_proxy_async_smem();
         __syncwarp();
         const int64_t ev = int64_t(cnt) * K;  // elements of the sph tile
-        int64_t ev_bulk = 0, ed_bulk = 0;
+        int64_t ev_bulk = 0, ed_bulk = 0, eh_bulk = 0;
         if (bulk) {
             ev_bulk = (ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
             ed_bulk = GRAD ? (3 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO)) : 0;
+            eh_bulk = HESS ? (9 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO)) : 0;
             if (lane == 0) {
                 if (ev_bulk) bulk_store(sph + p0 * K, s_v, uint32_t(ev_bulk * sizeof(TO)));
                 if (GRAD && ed_bulk) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * sizeof(TO)));
+                if (HESS && eh_bulk) bulk_store(ddsph + p0 * 9 * K, s_h, uint32_t(eh_bulk * sizeof(TO)));
                 bulk_commit();
             }
         }
@@ -269,6 +289,8 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
         for (int64_t i = ev_bulk + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
         if (GRAD)
             for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
+        if (HESS)
+            for (int64_t i = eh_bulk + lane; i < 9 * ev; i += 32) ddsph[p0 * 9 * K + i] = s_h[i];
         if (bulk && lane == 0) bulk_wait_read_all();
         __syncwarp();
     }
@@ -515,20 +537,22 @@ inline int grid_for(K kern, int threads, size_t smem, int64_t work_warps, int bl
     return int(std::max<int64_t>(1, std::min(want, cap)));
 }
 
-template <int L, bool GRAD, bool NORM, typename T, typename TO>
+template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO>
 int launch_point_fwd(const FwdArgs& a) {
-    static const PointTabs<L, T, false> tb = make_point_tabs<L, T, false>();
+    static const PointTabs<L, T, HESS> tb = make_point_tabs<L, T, HESS>();
     const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
-    const size_t smem = size_t(W) * point_fwd_warp_bytes<L, GRAD, TO>(P);
-    auto kern = point_fwd_kernel<L, GRAD, NORM, T, TO>;
+    const size_t smem = size_t(W) * point_fwd_warp_bytes<L, GRAD, HESS, TO>(P);
+    auto kern = point_fwd_kernel<L, GRAD, HESS, NORM, T, TO>;
     cudaError_t err = ensure_smem(kern, smem);
     if (err != cudaSuccess) return int(err);
     const int64_t ntiles = ceil_div(a.n, P);
     const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
     const bool bulk = (reinterpret_cast<uintptr_t>(a.sph) % 16 == 0) &&
-                      (!GRAD || reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0);
+                      (!GRAD || reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0) &&
+                      (!HESS || reinterpret_cast<uintptr_t>(a.ddsph) % 16 == 0);
     kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
-        static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph), P, bulk ? 1 : 0);
+        static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph),
+        static_cast<TO*>(a.ddsph), P, bulk ? 1 : 0);
     return int(cudaGetLastError());
 }
 

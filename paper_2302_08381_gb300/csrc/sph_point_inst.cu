@@ -16,11 +16,18 @@ int SPH_CAT(point_fwd_L, SPH_INST_L)(const FwdArgs& a) {
     constexpr int L = SPH_INST_L;
     const bool grad = a.dsph != nullptr;
     const bool norm = a.normalized != 0;
-#define SPH_FWD(T, TO)                                                   \
-    return grad ? (norm ? launch_point_fwd<L, true, true, T, TO>(a)      \
-                        : launch_point_fwd<L, true, false, T, TO>(a))    \
-                : (norm ? launch_point_fwd<L, false, true, T, TO>(a)     \
-                        : launch_point_fwd<L, false, false, T, TO>(a));
+#define SPH_FWD(T, TO)                                                          \
+    return grad ? (norm ? launch_point_fwd<L, true, false, true, T, TO>(a)      \
+                        : launch_point_fwd<L, true, false, false, T, TO>(a))    \
+                : (norm ? launch_point_fwd<L, false, false, true, T, TO>(a)     \
+                        : launch_point_fwd<L, false, false, false, T, TO>(a));
+    if (a.ddsph != nullptr) {  // Hessians (FP32 or FP64 storage; validated by the caller)
+        if (a.dtype == SPH_F64)
+            return norm ? launch_point_fwd<L, true, true, true, double, double>(a)
+                        : launch_point_fwd<L, true, true, false, double, double>(a);
+        return norm ? launch_point_fwd<L, true, true, true, float, float>(a)
+                    : launch_point_fwd<L, true, true, false, float, float>(a);
+    }
     if (a.dtype == SPH_F64) {
         SPH_FWD(double, double)
     }

@@ -33,13 +33,13 @@ PointFwdFn point_fwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kFwd[
 PointBwdFn point_bwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kBwd[L] : nullptr; }
 PointBwdFn point_dbwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kDbwd[L] : nullptr; }
 
-size_t point_row_bytes(int L, int grad, int elem) {
+size_t point_row_bytes(int L, int grad, int elem, int hess) {
     // Shared-memory bytes of one point's staged outputs: rows padded to an
     // odd stride when K is even (see RowStride in sph_point.cuh).
     const size_t K = size_t(L + 1) * size_t(L + 1);
     const bool pad = (K % 2 == 0);
-    const size_t v = pad ? K + 1 : K, d = pad ? 3 * K + 1 : 3 * K;
-    return size_t(elem) * (v + (grad ? d : 0));
+    const size_t v = pad ? K + 1 : K, d = pad ? 3 * K + 1 : 3 * K, h = pad ? 9 * K + 1 : 9 * K;
+    return size_t(elem) * (v + ((grad || hess) ? d : 0) + (hess ? h : 0));
 }
 
 }  // namespace sph

@@ -181,7 +181,7 @@ int sphericart_tune_export(char* buf, size_t len, size_t* needed) {
     for (int L = 0; L <= SPH_MAX_L_POINT; ++L)
         for (int dt = 0; dt <= 1; ++dt)
             for (int out = 0; out <= 1; ++out)
-                for (int grad = 0; grad <= 1; ++grad) {
+                for (int grad = 0; grad <= 2; ++grad) {
                     if (dt == SPH_F64 && out == SPH_OUT_BF16) continue;
                     int fam = 0;
                     sph_launch s{0, 0, 0, 0};

@@ -76,14 +76,16 @@ def test_double_backward_matches_oracle(kernel, normalized, l_max):
     assert _rel(gx32.cpu().numpy(), rgx, floor) < 1e-4
 
 
-def test_hessian_output_slice():
-    """ddsph of the SLICE forward vs the oracle, plus exact invariants:
+@pytest.mark.parametrize("kernel", ["point", "slice"])
+def test_hessian_output(kernel):
+    """ddsph of the forward vs the oracle, plus exact invariants:
     symmetric, trace-free (solid harmonics are harmonic), Euler relation."""
     n = 300
     x = inputs.shell_points(n, 0.7, 2.0, seed=206).astype(np.float64)
     lv = None
-    for l_max in (0, 1, 2, 5, 9, 20):
-        sph, dsph, ddsph = api.spherical_harmonics(_t(x, torch.float64), l_max, gradients=True, hessians=True)
+    for l_max in (0, 1, 2, 5, 8, 9, 16) + ((20,) if kernel == "slice" else ()):
+        sph, dsph, ddsph = api.spherical_harmonics(_t(x, torch.float64), l_max, gradients=True, hessians=True,
+                                                   kernel=kernel)
         H = ddsph.cpu().numpy()
         G = dsph.cpu().numpy()
         ref = oracle.spherical_harmonics_hessian(x, l_max)
@@ -96,10 +98,28 @@ def test_hessian_output_slice():
         euler = np.einsum("nj,nijk->nik", x, H) - (lv[None, None, :] - 1.0) * G
         assert np.max(np.abs(euler) / hs[:, None, :]) < 1e-11, l_max
         # normalized Hessians against the oracle
-        _, _, Hn = api.spherical_harmonics(_t(x, torch.float64), l_max, True, hessians=True)
+        _, _, Hn = api.spherical_harmonics(_t(x, torch.float64), l_max, True, hessians=True, kernel=kernel)
         refn = oracle.spherical_harmonics_hessian(x, l_max, True)
         assert _rel(Hn.cpu().numpy(), refn, 1e-3) < 1e-7, l_max
+        # FP32 Hessians against the FP64 ones
+        _, _, H32 = api.spherical_harmonics(_t(x), l_max, gradients=True, hessians=True, kernel=kernel)
+        x32 = x.astype(np.float32).astype(np.float64)
+        ref32 = oracle.spherical_harmonics_hessian(x32, l_max)
+        assert np.max(np.abs(H32.double().cpu().numpy() - ref32) / hs[:, None, None, :]) < 5e-5, l_max
     del lv
+
+
+def test_hessian_point_matches_slice_and_tiles():
+    """POINT and SLICE Hessians agree (FP64); POINT over several tile shapes."""
+    n = 5003
+    x = _t(inputs.shell_points(n, 0.5, 3.0, seed=230), torch.float64)
+    for l_max in (3, 8):
+        a = api.spherical_harmonics(x, l_max, gradients=True, hessians=True, kernel="slice")
+        for P, W in ((2, 1), (4, 2), (8, 1)):
+            b = api.spherical_harmonics(x, l_max, gradients=True, hessians=True, kernel="point",
+                                        launch=C.make_launch(P, W, 1, 0))
+            for u, v in zip(a, b):
+                assert (u - v).abs().max().item() <= 1e-12 * max(1.0, u.abs().max().item()), (l_max, P, W)
 
 
 @pytest.mark.parametrize("l_max,normalized", [(3, False), (6, True), (8, False), (19, False)])

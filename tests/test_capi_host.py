@@ -109,10 +109,10 @@ def test_argument_errors_before_any_cuda_call():
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 9, launch, 16, none, none, none) == C.SPH_EINVAL
     # ddsph without dsph
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, 32, none) == C.SPH_EINVAL
-    # bf16 with FP64 arithmetic; POINT beyond its l_max, with Hessians, or mixed Q
+    # bf16 with FP64 arithmetic; POINT beyond its l_max, with bf16 Hessians, or mixed Q
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 1, 1, 0, 0, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 17, 0, 0, 0, 0, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
-    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 1, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 1, 0, 1, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 1, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
     # NULL required pointers
     assert _err(C.sphericart_compute_ex, none, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
