@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "bwd", "dbwd", "batch", "expansion"],
+        choices=["fwd", "bwd", "dbwd", "batch", "expansion", "slice20", "hess"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     args = ap.parse_args()
@@ -445,8 +445,10 @@ def run_profile(args):
         _build.build()
     dev = torch.device("cuda", 0)
     n = args.n
-    if args.profile in ("fwd", "batch"):
+    if args.profile in ("fwd", "batch", "hess"):
         L = L_MAX
+    elif args.profile == "slice20":
+        L = 20
     else:
         L = BWD_L  # backward kernels and the expansion: l_max = 6
     K = (L + 1) ** 2
@@ -455,6 +457,10 @@ def run_profile(args):
         sph = torch.empty((n, K), device=dev)
         dsph = torch.empty((n, 3, K), device=dev)
         fn = lambda: api.spherical_harmonics(x, L, False, gradients=True, out=(sph, dsph))  # noqa: E731
+    elif args.profile == "slice20":
+        fn = lambda: api.spherical_harmonics(x, L, True, gradients=True)  # noqa: E731
+    elif args.profile == "hess":
+        fn = lambda: api.spherical_harmonics(x, L, gradients=True, hessians=True)  # noqa: E731
     elif args.profile in ("bwd", "dbwd"):
         g = torch.from_numpy(inputs.upstream(n, K, seed=33)).to(dev)
         v = torch.from_numpy(inputs.upstream(n, 3, seed=34)).to(dev)
@@ -603,6 +609,22 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
 
         def fn():
             api.spherical_harmonics(x, L, **kw)
+
+        # POINT-family forward variants use the library's autotuner too (as the
+        # headline does); value-only / gradient / bf16 / FP64 shapes are tuned
+        # separately, Hessian shapes keep their defaults.
+        if L <= 16 and "kernel" not in kw and "qprec" not in kw and not kw.get("hessians"):
+            from paper_2302_08381_gb300 import _capi as C
+
+            sph = torch.empty((n, K), dtype=kw.get("out_dtype", dt) or dt, device=dev)
+            dsph = torch.empty((n, 3, K), dtype=sph.dtype, device=dev) if kw.get("gradients") else None
+            C.sphericart_autotune(
+                x.data_ptr(), n, L, 1 if kw.get("normalized") else 0,
+                C.SPH_F64 if dt == torch.float64 else C.SPH_F32,
+                C.SPH_OUT_BF16 if kw.get("out_dtype") == torch.bfloat16 else C.SPH_OUT_SAME,
+                sph.data_ptr(), dsph.data_ptr() if dsph is not None else None, stream.cuda_stream, 2,
+            )
+            del sph, dsph
 
         for _ in range(3):
             fn()
