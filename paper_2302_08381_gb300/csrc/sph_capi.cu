@@ -79,16 +79,30 @@ const void* device_tables(int dtype) {
     if (slot) return slot;
     const HostTables& h = host_tables();
     const int tn = tri_size(SPH_MAX_L);
-    const std::vector<double>* src[kSliceTables] = {&h.qll, &h.d, &h.a, &h.b, &h.e, &h.fz, &h.g2, &h.g3, &h.g4};
+    // Packed per-(l, m) entries of kSliceTables values, see sph_internal.h:
+    //   [0] a (m <= l-2), d_l (m = l-1), 0 (m = l)   [1] b (m <= l-2), else 0
+    //   [2] Qtilde_l^l on the diagonal, else 0        [3] e
+    //   [4] f   [5] g2   [6] g3   [7] g4
     const size_t elem = (dtype == SPH_F64) ? 8 : 4;
     std::vector<unsigned char> host(size_t(kSliceTables) * tn * elem);
-    for (int t = 0; t < kSliceTables; ++t)
-        for (int i = 0; i < tn; ++i) {
-            const double v = (*src[t])[i];
-            if (dtype == SPH_F64)
-                reinterpret_cast<double*>(host.data())[size_t(t) * tn + i] = v;
-            else
-                reinterpret_cast<float*>(host.data())[size_t(t) * tn + i] = static_cast<float>(v);
+    for (int l = 0; l <= SPH_MAX_L; ++l)
+        for (int m = 0; m <= l; ++m) {
+            const int i = tri(l, m);
+            const double v[kSliceTables] = {m <= l - 2 ? h.a[i] : (m == l - 1 ? h.d[i] : 0.0),
+                                            m <= l - 2 ? h.b[i] : 0.0,
+                                            m == l ? h.qll[i] : 0.0,
+                                            h.e[i],
+                                            h.fz[i],
+                                            h.g2[i],
+                                            h.g3[i],
+                                            h.g4[i]};
+            for (int t = 0; t < kSliceTables; ++t) {
+                const size_t o = size_t(i) * kSliceTables + t;
+                if (dtype == SPH_F64)
+                    reinterpret_cast<double*>(host.data())[o] = v[t];
+                else
+                    reinterpret_cast<float*>(host.data())[o] = static_cast<float>(v[t]);
+            }
         }
     void* p = nullptr;
     if (cudaMalloc(&p, host.size()) != cudaSuccess) {

@@ -40,9 +40,12 @@ struct HostTables {
 
 const HostTables& host_tables();
 
-// Number of per-(l,m) tables packed for the SLICE kernels, in this order:
-// qll, d, a, b, e, fz, g2, g3, g4.
-constexpr int kSliceTables = 9;
+// Values per (l, m) entry of the packed SLICE tables (entry-major, two
+// 4-vectors per entry): {A, B, S, e} and {f, g2, g3, g4}, where the Q
+// recursion of channel m reads Qtilde_l^m = A z Qtilde_{l-1}^m
+// - B r^2 Qtilde_{l-2}^m + S with A = a, B = b for m <= l-2, A = d_l, B = 0
+// for m = l-1, and S = Qtilde_l^l, A = B = 0 on the diagonal.
+constexpr int kSliceTables = 8;
 
 // Device copy of the packed tables for the current device, FP32 or FP64.
 // Returns nullptr and sets the error message on failure.

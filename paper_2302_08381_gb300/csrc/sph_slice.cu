@@ -23,16 +23,27 @@ namespace sph {
 
 namespace {
 
-enum { TQLL = 0, TD = 1, TA = 2, TB = 3, TE = 4, TFZ = 5, TG2 = 6, TG3 = 7, TG4 = 8 };
-
-// Qtilde_l^c of channel c at degree l from its two previous values.
 template <typename TQ>
-__device__ __forceinline__ TQ advance(const TQ* __restrict__ tb, int tn, int l, int c, TQ z, TQ r2, TQ q1, TQ q2) {
-    if (l < c) return TQ(0);
-    if (l == c) return tb[TQLL * tn + tri(l, l)];
-    if (l == c + 1) return tb[TD * tn + tri(l, l - 1)] * z * q1;
-    const int i = tri(l, c);
-    return (tb[TA * tn + i] * z) * q1 - (tb[TB * tn + i] * r2) * q2;
+struct V4T;
+template <>
+struct V4T<float> {
+    using type = float4;
+};
+template <>
+struct V4T<double> {
+    using type = double4_32a;  // entries are 64-byte strided, so 32-byte aligned
+};
+
+// Qtilde_l^c of channel c at degree l from its two previous values, with one
+// vector load and no branch: the packed entry folds the diagonal seed and the
+// first off-diagonal step into the same formula; l < c gives 0.
+template <typename TQ>
+__device__ __forceinline__ TQ advance(const TQ* __restrict__ tb, int l, int c, TQ z, TQ r2, TQ q1, TQ q2) {
+    using V4 = typename V4T<TQ>::type;
+    const bool on = l >= c;
+    const V4 t = reinterpret_cast<const V4*>(tb)[2 * tri(l, on ? c : l)];
+    const TQ q = (t.x * z) * q1 - (t.y * r2) * q2 + t.z;
+    return on ? q : TQ(0);
 }
 
 // Visits every column of the lane's channels at one point. For each (l, m)
@@ -63,6 +74,8 @@ __device__ __forceinline__ Deriv<T> to_type(const Deriv<TQ>& d) {
 template <typename TQ, typename T, bool GRAD, bool HESS, bool NORM, int G, typename F>
 __device__ __forceinline__ void slice_point(T xin, T yin, T zin, int L, int j, const TQ* __restrict__ tb, int tn,
                                             TQ inv_sqrt2, bool active, F&& f) {
+    using V4 = typename V4T<TQ>::type;
+    (void)tn;
     TQ xq = TQ(xin), yq = TQ(yin), zq = TQ(zin);
     TQ r2q, irq = TQ(1);
     if (NORM) {
@@ -87,25 +100,27 @@ __device__ __forceinline__ void slice_point(T xin, T yin, T zin, int L, int j, c
         }
         TQ a1 = TQ(0), a2 = TQ(0), b1 = TQ(0), b2 = TQ(0), c1 = TQ(0), c2 = TQ(0);
         for (int l = m0; l <= L; ++l) {
-            const TQ qa = advance(tb, tn, l, m, zq, r2q, a1, a2);
-            const TQ qb = (GRAD || HESS) ? advance(tb, tn, l, m + 1, zq, r2q, b1, b2) : TQ(0);
-            const TQ qc = HESS ? advance(tb, tn, l, m + 2, zq, r2q, c1, c2) : TQ(0);
+            const TQ qa = advance(tb, l, m, zq, r2q, a1, a2);
+            const TQ qb = (GRAD || HESS) ? advance(tb, l, m + 1, zq, r2q, b1, b2) : TQ(0);
+            const TQ qc = HESS ? advance(tb, l, m + 2, zq, r2q, c1, c2) : TQ(0);
             if (active && m <= l) {
                 const int i = tri(l, m);
                 QParts<TQ> qp;
                 qp.Q = qa;
                 if (GRAD || HESS) {
-                    qp.E1 = tb[TE * tn + i] * b1;
-                    qp.Qz = tb[TFZ * tn + i] * a1;
+                    const V4 t0 = reinterpret_cast<const V4*>(tb)[2 * i];
+                    const V4 t1 = reinterpret_cast<const V4*>(tb)[2 * i + 1];
+                    qp.E1 = t0.w * b1;
+                    qp.Qz = t1.x * a1;
+                    if (HESS) {
+                        qp.G2 = t1.y * c2;
+                        qp.G3 = t1.z * b2;
+                        qp.G4 = t1.w * a2;
+                    } else {
+                        qp.G2 = qp.G3 = qp.G4 = TQ(0);
+                    }
                 } else {
-                    qp.E1 = qp.Qz = TQ(0);
-                }
-                if (HESS) {
-                    qp.G2 = tb[TG2 * tn + i] * c2;
-                    qp.G3 = tb[TG3 * tn + i] * b2;
-                    qp.G4 = tb[TG4 * tn + i] * a2;
-                } else {
-                    qp.G2 = qp.G3 = qp.G4 = TQ(0);
+                    qp.E1 = qp.Qz = qp.G2 = qp.G3 = qp.G4 = TQ(0);
                 }
                 if (m == 0) {
                     Deriv<TQ> d = assemble_m0<GRAD, HESS>(qp, xq, yq, inv_sqrt2);
