@@ -501,3 +501,39 @@ def test_expansion_power_spectrum_is_rotation_invariant():
         cr_bad[:, :, 4:9] = cr[:, :, 4:9] + 0.3 * cr[:, :, 0:1]
         assert not np.allclose(_wigner_free_power_spectrum(c_bad, l_max),
                                _wigner_free_power_spectrum(cr_bad, l_max), rtol=1e-6)
+
+
+# --------------------------------------------------------------- readings of the paper
+def test_downward_m_recursion_sign_reading():
+    """Eq. iter-q-alt as printed has the wrong sign; the reading taken is
+    Q_l^m = -[2(m+1) z Q_l^{m+1} + r_xy^2 Q_l^{m+2}] / ((l+m+1)(l-m)).
+    Checked on Q_l^m = r^l r_xy^-m P_l^m built from the oracle's Legendre table."""
+    xyz = inputs.shell_points(40, 0.6, 2.0, seed=50, dtype=np.float64)
+    x, y, z = xyz.T
+    r = np.linalg.norm(xyz, axis=1)
+    rxy = np.hypot(x, y)
+    l_max = 8
+    P, _ = orc.legendre_table(l_max, z / r, rxy / r)
+    Q = {(l, m): r**l * rxy ** (-m) * P[l, m] for l in range(l_max + 1) for m in range(l + 1)}
+    for l in range(1, l_max + 1):
+        for m in range(0, l - 1):
+            q2 = Q[(l, m + 2)] if m + 2 <= l else 0.0
+            corrected = -(2 * (m + 1) * z * Q[(l, m + 1)] + rxy**2 * q2) / ((l + m + 1) * (l - m))
+            printed = (2 * (m + 1) * z * Q[(l, m + 1)] + rxy**2 * q2) / ((l + m + 1) * (l - m))
+            np.testing.assert_allclose(corrected, Q[(l, m)], rtol=1e-10, atol=1e-10)
+            assert not np.allclose(printed, Q[(l, m)], rtol=1e-6), (l, m)
+    # Q_1^0 = z: the printed form would give -z
+    np.testing.assert_allclose(Q[(1, 0)], z, rtol=1e-13)
+
+
+def test_direct_z_link_reading():
+    """The direct link printed with swapped indices reads, with |m|,
+    d/dz Ytilde_l^m = (F_l^|m| / F_{l-1}^|m|) (l + |m|) Ytilde_{l-1}^m."""
+    xyz = inputs.shell_points(30, 0.6, 2.0, seed=51, dtype=np.float64)
+    l_max = 7
+    V, G = spherical_harmonics_grad(xyz, l_max)
+    for l in range(1, l_max + 1):
+        for m in range(-(l - 1), l):
+            am = abs(m)
+            coef = prefactor(l, am) / prefactor(l - 1, am) * (l + am)
+            np.testing.assert_allclose(G[:, 2, column(l, m)], coef * V[:, column(l - 1, m)], rtol=1e-11, atol=1e-12)
