@@ -759,6 +759,7 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     out["batch"] = run_batch_leg(torch, np, api, inputs, dev, stream, flush)
     out["expansion"] = run_expansion_leg(torch, np, api, inputs, dev, stream, flush)
     bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
+    dbwd_bytes = BWD_N * (12 + Kb * 4 + 12 + Kb * 4 + 12)
     out["backward"] = {
         "workload": f"N={BWD_N}, l_max={Lb}, |r|~U[0.7,6], g~N(0,1), FP32",
         "fused_fwd_plus_bwd_ms": t_fused,
@@ -767,6 +768,7 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
         "fused_bwd_kernel_ms": t_bwd,
         "fused_bwd_achieved_GBs": bwd_bytes / (t_bwd * 1e-3) / 1e9,
         "double_backward_ms": t_dbwd,
+        "double_backward_achieved_GBs": dbwd_bytes / (t_dbwd * 1e-3) / 1e9,
         "max_rel_diff_fused_vs_plain": diff,
         "stated_error": "both within 2e-5 (max-relative) of the FP64 oracle on sampled points of this "
         "workload and within 1e-5 of central differences (h=1e-3, FP64): tests/test_backward_gpu.py",

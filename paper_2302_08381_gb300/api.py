@@ -233,6 +233,37 @@ def materialized_expansion(xyz, radial, offsets, l_max, normalized=False):
     return out.index_add_(0, centre, contrib)
 
 
+def autotune(xyz, l_max, normalized=False, gradients=True, out_dtype=None, reps=3):
+    """Runs the library's autotuner for this forward request on the current
+    device (outputs are scratch) and installs the fastest launch shape for
+    later calls. Returns (shape dict, best ms)."""
+    _check_points(xyz)
+    K = n_columns(l_max)
+    odt = torch.bfloat16 if out_dtype == torch.bfloat16 else xyz.dtype
+    sph = torch.empty((xyz.shape[0], K), dtype=odt, device=xyz.device)
+    dsph = torch.empty((xyz.shape[0], 3, K), dtype=odt, device=xyz.device) if gradients else None
+    best, ms = C.sphericart_autotune(
+        xyz.data_ptr(), xyz.shape[0], l_max, 1 if normalized else 0, _dtype_code(xyz),
+        C.SPH_OUT_BF16 if odt == torch.bfloat16 else C.SPH_OUT_SAME, sph.data_ptr(),
+        dsph.data_ptr() if dsph is not None else None, _stream(xyz.device), reps,
+    )
+    return {"points_per_tile": best.points_per_tile, "warps_per_block": best.warps_per_block,
+            "blocks_per_sm": best.blocks_per_sm}, ms
+
+
+def save_tuning(path: str) -> None:
+    """Writes the tuned launch shapes of the current device (keyed by GPU name)."""
+    with open(path, "w") as f:
+        f.write(C.sphericart_tune_export())
+
+
+def load_tuning(path: str) -> int:
+    """Installs the shapes of a saved table whose GPU name matches the current
+    device; returns how many were installed."""
+    with open(path) as f:
+        return C.sphericart_tune_import(f.read())
+
+
 def device_status() -> int:
     """Reads and clears the device status word (nonzero: a bounded wait timed out)."""
     return C.sphericart_device_status()

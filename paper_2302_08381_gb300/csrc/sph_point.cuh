@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -513,22 +514,70 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
 // ---------------------------------------------------------------- launchers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Per-kernel, per-device cache of host-side launch facts, so a launch costs
+// no driver queries after the first (small launches are latency-bound).
+struct LaunchCache {
+    static constexpr int kDev = 64;
+    std::atomic<int> smem_set[kDev];       // largest dynamic smem size set
+    std::atomic<long long> occ_key[kDev];  // (threads << 32) | smem of the cached occupancy
+    std::atomic<int> occ[kDev];
+    LaunchCache() {
+        for (int i = 0; i < kDev; ++i) {
+            smem_set[i] = 48 * 1024;
+            occ_key[i] = -1;
+            occ[i] = 0;
+        }
+    }
+};
+
+template <typename K>
+inline LaunchCache& launch_cache(K) {
+    static LaunchCache c;  // one per kernel instantiation
+    return c;
+}
+
+inline int cache_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= LaunchCache::kDev) return -1;
+    return d;
+}
+
 // Raise the dynamic shared-memory limit of `kern` once per device and size.
 template <typename K>
 inline cudaError_t ensure_smem(K kern, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(bytes));
+    const int d = cache_device();
+    LaunchCache& c = launch_cache(kern);
+    if (d >= 0 && c.smem_set[d].load() >= int(bytes)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess && d >= 0) {
+        int cur = c.smem_set[d].load();
+        while (cur < int(bytes) && !c.smem_set[d].compare_exchange_weak(cur, int(bytes))) {
+        }
+    }
+    return e;
 }
 
 template <typename K>
 inline int grid_for(K kern, int threads, size_t smem, int64_t work_warps, int blocks_per_sm) {
     int bps = blocks_per_sm;
     if (bps <= 0) {
+        const int d = cache_device();
+        LaunchCache& c = launch_cache(kern);
+        const long long key = (static_cast<long long>(threads) << 32) | static_cast<long long>(smem);
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), threads,
-                                                          smem) != cudaSuccess)
-            occ = 1;
+        if (d >= 0 && c.occ_key[d].load() == key) {
+            occ = c.occ[d].load();
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), threads,
+                                                              smem) != cudaSuccess)
+                occ = 1;
+            if (d >= 0) {
+                c.occ[d] = occ;
+                c.occ_key[d] = key;
+            }
+        }
         bps = std::max(occ, 1);
     }
     const int W = threads / 32;

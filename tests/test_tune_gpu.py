@@ -61,3 +61,12 @@ def test_batch_autotune_returns_a_plan_shape():
     torch.cuda.synchronize()
     for a, b in zip(tuned.sph, plan.sph):
         assert torch.allclose(a, b, rtol=1e-6, atol=1e-6)
+
+
+def test_tuning_save_and_load_roundtrip(tmp_path):
+    x = torch.from_numpy(inputs.shell_points(50_000, 0.5, 5.0, seed=402)).to(DEV)
+    shape, ms = api.autotune(x, 6, reps=1)
+    assert ms > 0 and shape["points_per_tile"] > 0
+    path = tmp_path / "tune.txt"
+    api.save_tuning(str(path))
+    assert api.load_tuning(str(path)) >= 1
