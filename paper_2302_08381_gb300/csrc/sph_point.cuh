@@ -19,9 +19,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "sph_core.cuh"
 #include "sph_internal.h"
@@ -514,31 +515,32 @@ __global__ void __launch_bounds__(256) point_bwd_kernel(const T* __restrict__ xy
 // ---------------------------------------------------------------- launchers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Per-kernel, per-device cache of host-side launch facts, so a launch costs
-// no driver queries after the first (small launches are latency-bound).
-struct LaunchCache {
-    static constexpr int kDev = 64;
-    std::atomic<int> smem_set[kDev];       // largest dynamic smem size set
-    std::atomic<long long> occ_key[kDev];  // (threads << 32) | smem of the cached occupancy
-    std::atomic<int> occ[kDev];
-    LaunchCache() {
-        for (int i = 0; i < kDev; ++i) {
-            smem_set[i] = 48 * 1024;
-            occ_key[i] = -1;
-            occ[i] = 0;
-        }
-    }
+// Host-side launch cache, keyed by (kernel address, device): the largest
+// dynamic shared-memory size already set on the kernel and the occupancy of
+// the last (threads, smem) pair queried, so repeated launches skip the
+// attribute call and the occupancy query.
+struct LaunchEntry {
+    int smem_set = 48 * 1024;
+    long long occ_key = -1;  // (threads << 32) | smem of `occ`
+    int occ = 0;
 };
 
-template <typename K>
-inline LaunchCache& launch_cache(K) {
-    static LaunchCache c;  // one per kernel instantiation
-    return c;
+inline std::mutex& launch_cache_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+inline LaunchEntry& launch_entry(const void* kern, int dev) {  // caller holds the mutex
+    static std::map<std::pair<const void*, int>, LaunchEntry> cache;
+    return cache[std::make_pair(kern, dev)];
 }
 
 inline int cache_device() {
     int d = 0;
-    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= LaunchCache::kDev) return -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
     return d;
 }
 
@@ -546,16 +548,12 @@ inline int cache_device() {
 template <typename K>
 inline cudaError_t ensure_smem(K kern, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
+    const void* f = reinterpret_cast<const void*>(kern);
     const int d = cache_device();
-    LaunchCache& c = launch_cache(kern);
-    if (d >= 0 && c.smem_set[d].load() >= int(bytes)) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    if (e == cudaSuccess && d >= 0) {
-        int cur = c.smem_set[d].load();
-        while (cur < int(bytes) && !c.smem_set[d].compare_exchange_weak(cur, int(bytes))) {
-        }
-    }
+    std::lock_guard<std::mutex> lk(launch_cache_mutex());
+    if (d >= 0 && launch_entry(f, d).smem_set >= int(bytes)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess && d >= 0) launch_entry(f, d).smem_set = int(bytes);
     return e;
 }
 
@@ -563,19 +561,22 @@ template <typename K>
 inline int grid_for(K kern, int threads, size_t smem, int64_t work_warps, int blocks_per_sm) {
     int bps = blocks_per_sm;
     if (bps <= 0) {
+        const void* f = reinterpret_cast<const void*>(kern);
         const int d = cache_device();
-        LaunchCache& c = launch_cache(kern);
         const long long key = (static_cast<long long>(threads) << 32) | static_cast<long long>(smem);
         int occ = 0;
-        if (d >= 0 && c.occ_key[d].load() == key) {
-            occ = c.occ[d].load();
+        std::lock_guard<std::mutex> lk(launch_cache_mutex());
+        LaunchEntry* c = d >= 0 ? &launch_entry(f, d) : nullptr;
+        if (c && c->occ_key == key) {
+            occ = c->occ;
         } else {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), threads,
-                                                              smem) != cudaSuccess)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, threads, smem) != cudaSuccess) {
+                cudaGetLastError();
                 occ = 1;
-            if (d >= 0) {
-                c.occ[d] = occ;
-                c.occ_key[d] = key;
+            }
+            if (c) {
+                c->occ = occ;
+                c->occ_key = key;
             }
         }
         bps = std::max(occ, 1);
