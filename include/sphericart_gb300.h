@@ -73,17 +73,35 @@ typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
  * outputs but runs the unit-vector scaling, the c_m/s_m (Eq. iter-sc) and
  * Q_l^m (Eq. iter-q) recursions and the assembly in FP64, rounding once on
  * store. Measured: FP32 error at high l_max comes from rounding u = xyz/r and
- * the c_m/s_m powers, not from the Q recursion alone. SLICE kernels only. */
+ * the c_m/s_m powers, not from the Q recursion alone. SLICE and DEGREE
+ * kernels. */
 typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
-/* Kernel family. AUTO picks POINT when l_max <= SPH_MAX_L_POINT (except for
- * the mixed precision mode and bfloat16 Hessians), else SLICE.
- *   POINT: one thread per point, the whole (l, m) recursion unrolled in
- *          registers for a compile-time l_max, outputs staged in shared memory
- *          and written with bulk (TMA) copies.
- *   SLICE: a group of lanes per point, each lane owning the m channels
- *          m = j, j+G, ...; any l_max <= SPH_MAX_L; direct coalesced stores. */
-typedef enum { SPH_KERNEL_AUTO = 0, SPH_KERNEL_POINT = 1, SPH_KERNEL_SLICE = 2 } sph_kernel;
+/* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
+ * arithmetic (SPH_F64 or the mixed mode) without Hessians; else POINT when
+ * l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else DEGREE for
+ * bfloat16 storage without Hessians; else SLICE.
+ *   POINT:  one thread per point, the whole (l, m) recursion unrolled in
+ *           registers for a compile-time l_max, outputs staged in shared memory
+ *           and written with bulk (TMA) copies.
+ *   SLICE:  a group of lanes per point, each lane owning the m channels
+ *           m = j, j+G, ...; any l_max <= SPH_MAX_L; direct coalesced stores.
+ *   DEGREE: one thread per point with the degree l outermost at run time (any
+ *           l_max <= SPH_MAX_L): the Q columns of the previous two degrees
+ *           (Eq. iter-q) sit in shared memory, each degree's columns are staged
+ *           and stored by the warp with coalesced row-segment stores. Values
+ *           and gradients (no Hessians, no backward).
+ *   DEGREE_DOWN: as DEGREE, with Q_l^m of each degree by the downward-in-m
+ *           recursion of Eq. iter-q-alt (its printed overall sign corrected:
+ *           Q_l^m = -[2(m+1) z Q_l^{m+1} + (x^2+y^2) Q_l^{m+2}]/((l+m+1)(l-m)))
+ *           from the tabulated Q_l^l; the paper's one-degree-at-a-time form. */
+typedef enum {
+    SPH_KERNEL_AUTO = 0,
+    SPH_KERNEL_POINT = 1,
+    SPH_KERNEL_SLICE = 2,
+    SPH_KERNEL_DEGREE = 3,
+    SPH_KERNEL_DEGREE_DOWN = 4
+} sph_kernel;
 
 #define SPH_MAX_L 128
 #define SPH_MAX_L_POINT 16
@@ -92,7 +110,9 @@ typedef enum { SPH_KERNEL_AUTO = 0, SPH_KERNEL_POINT = 1, SPH_KERNEL_SLICE = 2 }
  *   points_per_tile  points a warp computes per tile, 4..32, multiple of 4
  *   warps_per_block  independent warps per CTA, 1..8
  *   blocks_per_sm    resident CTAs per SM to size the persistent grid (0 = max)
- *   lanes_per_point  SLICE kernels only: 8, 16 or 32 (0 = by l_max)          */
+ *   lanes_per_point  SLICE kernels only: 8, 16 or 32 (0 = by l_max)
+ * DEGREE kernels read only warps_per_block (0..8, 0 = by shared memory) and
+ * blocks_per_sm; a warp always owns 32 points.                                */
 typedef struct {
     int32_t points_per_tile;
     int32_t warps_per_block;
@@ -116,7 +136,8 @@ int sphericart_compute(const float* xyz, int64_t n, int l_max, int normalized,
  *   out    sph_out storage of sph/dsph/ddsph (element size 4, 8 or 2 bytes)
  *   qprec  sph_qprec of the Q recursion (SPH_Q_F64 with SPH_F32 only)
  *   kernel sph_kernel family; POINT with l_max > SPH_MAX_L_POINT, with the
- *          mixed mode or with bfloat16 Hessians returns SPH_EUNSUPPORTED
+ *          mixed mode or with bfloat16 Hessians returns SPH_EUNSUPPORTED, and
+ *          so do the DEGREE families with ddsph
  *   launch NULL or a launch shape (zeros = default)
  * SPH_EUNSUPPORTED also for BF16 output with FP64 arithmetic. */
 int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
@@ -150,7 +171,8 @@ int sphericart_compute_host(const void* xyz_host, int64_t n, int l_max, int norm
  * contracts the dsph materialised by the forward pass (Section 3); that path
  * is sphericart_compute + a contraction.
  *   xyz [n,3], g [n,K], dxyz [n,3], all of `dtype` (device).
- * Errors as sphericart_compute_ex (kernel: AUTO, POINT or SLICE). */
+ * Errors as sphericart_compute_ex (kernel: AUTO, POINT or SLICE; the DEGREE
+ * families return SPH_EUNSUPPORTED). */
 int sphericart_backward(const void* xyz, const void* g, int64_t n, int l_max,
                         int normalized, int dtype, int kernel,
                         const sph_launch* launch, void* dxyz, void* stream);
@@ -258,6 +280,9 @@ int sphericart_max_l(int dtype, int qprec, int kernel);
  *         4: e_l^m = F_l^m / F_{l-1}^{m+1}       (d/dx, d/dy of Eq. iter-deri)
  *         5: f_l^m = (l+m) F_l^m / F_{l-1}^m     (d/dz of Eq. iter-deri)
  *         6: d_l   = (2l-1) F_l^{l-1}/F_{l-1}^{l-1} on entry (l, l-1)
+ *         7: al_l^m, 8: be_l^m  coefficients of the folded downward recursion
+ *            Qtilde_l^m = al z Qtilde_l^{m+1} - be (x^2+y^2) Qtilde_l^{m+2}
+ *            (Eq. iter-q-alt with its overall sign corrected)
  * Tables 4 and 5 carry the 1/sqrt2 of the m = 0 column folded in.
  * Returns SPH_EINVAL for a bad `which`, l_max or NULL out. */
 int sphericart_host_table(int l_max, int which, double* out);

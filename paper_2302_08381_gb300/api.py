@@ -9,7 +9,13 @@ import torch
 
 from . import _capi as C
 
-_KERNELS = {"auto": C.SPH_KERNEL_AUTO, "point": C.SPH_KERNEL_POINT, "slice": C.SPH_KERNEL_SLICE}
+_KERNELS = {
+    "auto": C.SPH_KERNEL_AUTO,
+    "point": C.SPH_KERNEL_POINT,
+    "slice": C.SPH_KERNEL_SLICE,
+    "degree": C.SPH_KERNEL_DEGREE,
+    "degree_down": C.SPH_KERNEL_DEGREE_DOWN,
+}
 _QPREC = {"native": C.SPH_Q_NATIVE, "f64": C.SPH_Q_F64}
 
 

@@ -48,6 +48,9 @@ def _units():
     units = []
     for l in range(MAX_L_POINT + 1):
         units.append(("sph_point_inst.cu", f"point_L{l}.o", [f"-DSPH_INST_L={l}"]))
+    units.append(("sph_degree.cu", "sph_degree_down.o", ["-DSPH_DEGREE_DOWN=1"]))
+    for lpp in (1, 2, 4):
+        units.append(("sph_degree.cu", f"sph_degree_up{lpp}.o", ["-DSPH_DEGREE_DOWN=0", f"-DSPH_DEGREE_LPP={lpp}"]))
     for src in ("sph_slice.cu", "sph_capi.cu", "sph_batch.cu", "sph_tune.cu", "sph_expansion.cu", "sph_host.cu", "sph_tables.cpp", "sph_point_registry.cpp"):
         units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units

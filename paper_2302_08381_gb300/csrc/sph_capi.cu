@@ -68,34 +68,21 @@ int max_smem_optin() {
     return g_smem[d];
 }
 
-const void* device_tables(int dtype) {
-    const int d = current_device();
-    if (d < 0) {
-        set_error("no current CUDA device");
-        return nullptr;
-    }
-    std::lock_guard<std::mutex> lk(g_mu);
-    void*& slot = (dtype == SPH_F64) ? g_tab64[d] : g_tab32[d];
+namespace {
+
+// Uploads kSliceTables values per (l, m) entry, produced by `pack`, as FP32 or
+// FP64 into `slot` (once per device).
+template <typename Pack>
+const void* upload_packed(void*& slot, int dtype, Pack pack) {
     if (slot) return slot;
-    const HostTables& h = host_tables();
     const int tn = tri_size(SPH_MAX_L);
-    // Packed per-(l, m) entries of kSliceTables values, see sph_internal.h:
-    //   [0] a (m <= l-2), d_l (m = l-1), 0 (m = l)   [1] b (m <= l-2), else 0
-    //   [2] Qtilde_l^l on the diagonal, else 0        [3] e
-    //   [4] f   [5] g2   [6] g3   [7] g4
     const size_t elem = (dtype == SPH_F64) ? 8 : 4;
     std::vector<unsigned char> host(size_t(kSliceTables) * tn * elem);
     for (int l = 0; l <= SPH_MAX_L; ++l)
         for (int m = 0; m <= l; ++m) {
             const int i = tri(l, m);
-            const double v[kSliceTables] = {m <= l - 2 ? h.a[i] : (m == l - 1 ? h.d[i] : 0.0),
-                                            m <= l - 2 ? h.b[i] : 0.0,
-                                            m == l ? h.qll[i] : 0.0,
-                                            h.e[i],
-                                            h.fz[i],
-                                            h.g2[i],
-                                            h.g3[i],
-                                            h.g4[i]};
+            double v[kSliceTables];
+            pack(l, m, i, v);
             for (int t = 0; t < kSliceTables; ++t) {
                 const size_t o = size_t(i) * kSliceTables + t;
                 if (dtype == SPH_F64)
@@ -116,6 +103,56 @@ const void* device_tables(int dtype) {
     }
     slot = p;
     return slot;
+}
+
+void* g_down32[kMaxDevices] = {nullptr};
+void* g_down64[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+const void* device_tables(int dtype) {
+    const int d = current_device();
+    if (d < 0) {
+        set_error("no current CUDA device");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    void*& slot = (dtype == SPH_F64) ? g_tab64[d] : g_tab32[d];
+    const HostTables& h = host_tables();
+    // Packed per-(l, m) entries of kSliceTables values, see sph_internal.h:
+    //   [0] a (m <= l-2), d_l (m = l-1), 0 (m = l)   [1] b (m <= l-2), else 0
+    //   [2] Qtilde_l^l on the diagonal, else 0        [3] e
+    //   [4] f   [5] g2   [6] g3   [7] g4
+    return upload_packed(slot, dtype, [&](int l, int m, int i, double* v) {
+        v[0] = m <= l - 2 ? h.a[i] : (m == l - 1 ? h.d[i] : 0.0);
+        v[1] = m <= l - 2 ? h.b[i] : 0.0;
+        v[2] = m == l ? h.qll[i] : 0.0;
+        v[3] = h.e[i];
+        v[4] = h.fz[i];
+        v[5] = h.g2[i];
+        v[6] = h.g3[i];
+        v[7] = h.g4[i];
+    });
+}
+
+const void* device_tables_down(int dtype) {
+    const int d = current_device();
+    if (d < 0) {
+        set_error("no current CUDA device");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    void*& slot = (dtype == SPH_F64) ? g_down64[d] : g_down32[d];
+    const HostTables& h = host_tables();
+    //   [0] al  [1] be  [2] Qtilde_l^l on the diagonal, else 0  [3] e  [4] f  [5..7] 0
+    return upload_packed(slot, dtype, [&](int l, int m, int i, double* v) {
+        v[0] = h.al[i];
+        v[1] = h.be[i];
+        v[2] = m == l ? h.qll[i] : 0.0;
+        v[3] = h.e[i];
+        v[4] = h.fz[i];
+        v[5] = v[6] = v[7] = 0.0;
+    });
 }
 
 uint32_t* device_status_word() {
@@ -248,6 +285,29 @@ bool valid_lanes(const sph_launch& s) {
 
 bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
+// Lanes per point of the upward DEGREE kernel when the caller leaves it 0
+// (measured on GB300: FP64 prefers 2 lanes per point up to l_max ~ 24 and 4
+// above, FP32 arithmetic with FP64 Q ("mixed") 2, FP32 / bf16 storage 4).
+int degree_default_lpp(int l_max, int dtype, int qprec) {
+    if (dtype == SPH_F64) return l_max >= 24 ? 4 : 2;
+    if (qprec == SPH_Q_F64) return 2;
+    return 4;
+}
+
+// AUTO kernel family of a forward request. POINT (compile-time l_max, TMA
+// bulk stores) wins whenever it applies in FP32; FP64 arithmetic (FP64 inputs
+// or the mixed mode) is bound by GB300's FP64 pipe, where the DEGREE family
+// (no idle lanes) is fastest at every measured l_max; beyond POINT's range,
+// bf16 storage is fastest on DEGREE and FP32 storage on SLICE; Hessians stay
+// on POINT / SLICE.
+int auto_family(int l_max, int dtype, int out, int qprec, bool hess) {
+    const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
+    if (!hess && (dtype == SPH_F64 || mixed)) return SPH_KERNEL_DEGREE;
+    if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
+    if (!hess && out == SPH_OUT_BF16) return SPH_KERNEL_DEGREE;
+    return SPH_KERNEL_SLICE;
+}
+
 int cuda_status(int err, const char* what) {
     if (err == 0) return SPH_OK;
     set_error("%s: %s", what, cudaGetErrorString(static_cast<cudaError_t>(err)));
@@ -268,7 +328,8 @@ int check_common(int64_t n, int l_max, int dtype, int kernel) {
         set_error("dtype=%d is not an sph_dtype", dtype);
         return SPH_EINVAL;
     }
-    if (kernel != SPH_KERNEL_AUTO && kernel != SPH_KERNEL_POINT && kernel != SPH_KERNEL_SLICE) {
+    if (kernel != SPH_KERNEL_AUTO && kernel != SPH_KERNEL_POINT && kernel != SPH_KERNEL_SLICE &&
+        kernel != SPH_KERNEL_DEGREE && kernel != SPH_KERNEL_DEGREE_DOWN) {
         set_error("kernel=%d is not an sph_kernel", kernel);
         return SPH_EINVAL;
     }
@@ -305,12 +366,12 @@ int sphericart_max_l(int dtype, int qprec, int kernel) {
 }
 
 int sphericart_host_table(int l_max, int which, double* out) {
-    if (!out || l_max < 0 || l_max > SPH_MAX_L || which < 0 || which > 6) {
+    if (!out || l_max < 0 || l_max > SPH_MAX_L || which < 0 || which > 8) {
         set_error("host_table: bad arguments (l_max=%d which=%d)", l_max, which);
         return SPH_EINVAL;
     }
     const HostTables& h = host_tables();
-    const std::vector<double>* src[] = {&h.F, &h.qll, &h.a, &h.b, &h.e, &h.fz, &h.d};
+    const std::vector<double>* src[] = {&h.F, &h.qll, &h.a, &h.b, &h.e, &h.fz, &h.d, &h.al, &h.be};
     std::memcpy(out, src[which]->data(), sizeof(double) * size_t(tri_size(l_max)));
     return SPH_OK;
 }
@@ -340,10 +401,14 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     const int grad = dsph ? 1 : 0;
     int fam = kernel;
     const bool hess_bf16 = ddsph && out == SPH_OUT_BF16;
-    if (fam == SPH_KERNEL_AUTO)
-        fam = (l_max <= SPH_MAX_L_POINT && !hess_bf16 && !mixed) ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE;
+    if (fam == SPH_KERNEL_AUTO) fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr);
     if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || hess_bf16 || mixed)) {
         set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
+        return SPH_EUNSUPPORTED;
+    }
+    const bool degree = fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN;
+    if (degree && ddsph) {
+        set_error("DEGREE kernels compute values and gradients only (Hessians: POINT or SLICE)");
         return SPH_EUNSUPPORTED;
     }
     if (n == 0) return SPH_OK;
@@ -376,6 +441,39 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
         if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo, hess))) return SPH_EINVAL;
         return cuda_status(point_fwd_fn(l_max)(a), "POINT forward launch");
     }
+    if (degree) {
+        if (a.launch.warps_per_block < 0 || a.launch.warps_per_block > 8 || a.launch.blocks_per_sm < 0 ||
+            a.launch.blocks_per_sm > 32) {
+            set_error("DEGREE launch: warps_per_block must be in [0,8] and blocks_per_sm in [0,32]");
+            return SPH_EINVAL;
+        }
+        const int lpp = a.launch.lanes_per_point;
+        if (lpp != 0 && lpp != 1 && lpp != 2 && lpp != 4) {
+            set_error("DEGREE launch: lanes_per_point must be 0, 1, 2 or 4");
+            return SPH_EINVAL;
+        }
+        if (fam == SPH_KERNEL_DEGREE_DOWN && lpp > 1) {
+            set_error("DEGREE_DOWN runs one lane per point (the downward recursion is sequential in m)");
+            return SPH_EINVAL;
+        }
+        int e;
+        if (fam == SPH_KERNEL_DEGREE_DOWN)
+            e = degree_fwd_down(a);
+        else if (lpp == 1)
+            e = degree_fwd_up1(a);
+        else if (lpp == 4)
+            e = degree_fwd_up4(a);
+        else if (lpp == 2)
+            e = degree_fwd_up2(a);
+        else
+            e = degree_default_lpp(l_max, dtype, qprec) == 1 ? degree_fwd_up1(a)
+                : degree_default_lpp(l_max, dtype, qprec) == 4 ? degree_fwd_up4(a) : degree_fwd_up2(a);
+        if (e == int(cudaErrorInvalidConfiguration)) {
+            set_error("DEGREE launch shape needs more shared memory per block than the device allows");
+            return SPH_EINVAL;
+        }
+        return cuda_status(e, "DEGREE forward launch");
+    }
     if (!valid_lanes(a.launch)) return SPH_EINVAL;
     return cuda_status(slice_fwd(a), "SLICE forward launch");
 }
@@ -394,6 +492,10 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
     int fam = kernel == SPH_KERNEL_AUTO ? (l_max <= SPH_MAX_L_POINT ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE) : kernel;
     if (fam == SPH_KERNEL_POINT && l_max > SPH_MAX_L_POINT) {
         set_error("POINT kernels take l_max <= %d", SPH_MAX_L_POINT);
+        return SPH_EUNSUPPORTED;
+    }
+    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN) {
+        set_error("backward passes run on the POINT or SLICE kernels");
         return SPH_EUNSUPPORTED;
     }
     if (n == 0) return SPH_OK;
@@ -470,7 +572,11 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         return SPH_EINVAL;
     }
     const int eo = elem_size(dtype, out);
-    if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) {
+    const int fam = auto_family(l_max, dtype, out, SPH_Q_NATIVE, hess != 0);
+    if (fam == SPH_KERNEL_DEGREE) {
+        *kernel_out = SPH_KERNEL_DEGREE;
+        *launch_out = sph_launch{0, 0, 0, degree_default_lpp(l_max, dtype, SPH_Q_NATIVE)};
+    } else if (fam == SPH_KERNEL_POINT) {
         *kernel_out = SPH_KERNEL_POINT;
         sph_launch s{0, 0, 0, 0};
         int d = -1;

@@ -35,6 +35,10 @@ struct HostTables {
     std::vector<double> g2;   // F_l^m/F_{l-2}^{m+2}                m <= l-4  (x 1/sqrt2 at m=0)
     std::vector<double> g3;   // (l+m) F_l^m/F_{l-2}^{m+1}          m <= l-3  (x 1/sqrt2 at m=0)
     std::vector<double> g4;   // (l+m)(l+m-1) F_l^m/F_{l-2}^m       m <= l-2  (x 1/sqrt2 at m=0)
+    // Downward-in-m recursion (Eq. iter-q-alt with its sign corrected, folded):
+    //   Qtilde_l^m = al z Qtilde_l^{m+1} - be (x^2+y^2) Qtilde_l^{m+2}
+    std::vector<double> al;   // -2(m+1)/((l+m+1)(l-m)) F_l^m/F_l^{m+1}   m <= l-1
+    std::vector<double> be;   // F_l^m/F_l^{m+2} / ((l+m+1)(l-m))        m <= l-2
     double inv_sqrt2 = 0.0;   // the 1/sqrt2 of the m = 0 column (Eq. real-sh-cartesian)
 };
 
@@ -50,6 +54,11 @@ constexpr int kSliceTables = 8;
 // Device copy of the packed tables for the current device, FP32 or FP64.
 // Returns nullptr and sets the error message on failure.
 const void* device_tables(int dtype);
+
+// Packed tables of the downward-in-m recursion for the DEGREE kernels
+// (entry-major, two 4-vectors per (l, m)): {al, be, S, e} and {f, 0, 0, 0},
+// S = Qtilde_l^l on the diagonal.
+const void* device_tables_down(int dtype);
 
 // Per-device status word written by kernels whose bounded waits time out.
 uint32_t* device_status_word();
@@ -108,6 +117,14 @@ bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s);
 
 // Bytes of one output row of the POINT forward for this request.
 size_t point_row_bytes(int L, int grad, int elem, int hess = 0);
+
+// DEGREE kernels (runtime l_max, degree outermost): Eq. iter-q upward in l
+// with 1, 2 or 4 lanes per point, or Eq. iter-q-alt downward in m (one lane
+// per point).
+int degree_fwd_up1(const FwdArgs& a);
+int degree_fwd_up2(const FwdArgs& a);
+int degree_fwd_up4(const FwdArgs& a);
+int degree_fwd_down(const FwdArgs& a);
 
 // SLICE kernels (runtime l_max).
 int slice_fwd(const FwdArgs& a);

@@ -19,6 +19,13 @@
 //      g4 = (l+m)(l+m-1) F_l^m/F_{l-2}^m.
 //  The derivative multipliers of the m = 0 column carry the 1/sqrt2 of
 //  Eq. real-sh-cartesian, so Ytilde_l^0 derivatives need no extra product.
+//  * Eq. iter-q-alt (downward in m at fixed l; the printed form has the wrong
+//    overall sign -- it gives Q_1^0 = -z -- and is used with the sign fixed):
+//      Q_l^m = -[2(m+1) z Q_l^{m+1} + (x^2+y^2) Q_l^{m+2}] / ((l+m+1)(l-m)),
+//    folded: Qtilde_l^m = al z Qtilde_l^{m+1} - be (x^2+y^2) Qtilde_l^{m+2},
+//      al = -2(m+1)/((l+m+1)(l-m)) F_l^m/F_l^{m+1},
+//      be = F_l^m/F_l^{m+2} / ((l+m+1)(l-m)),
+//    started from Qtilde_l^l (with Qtilde_l^{l+1} = 0).
 //  Q_l^l itself is never formed: Qtilde_l^l = -(2l-1)(F_l^l/F_{l-1}^{l-1}) Qtilde_{l-1}^{l-1}.
 #include <cmath>
 #include <mutex>
@@ -43,6 +50,8 @@ HostTables build_tables(int L) {
     t.g2.assign(n, 0.0);
     t.g3.assign(n, 0.0);
     t.g4.assign(n, 0.0);
+    t.al.assign(n, 0.0);
+    t.be.assign(n, 0.0);
     t.inv_sqrt2 = 1.0 / std::sqrt(2.0);
     const double two_pi = 2.0 * 3.14159265358979323846;
 
@@ -87,6 +96,9 @@ HostTables build_tables(int L) {
             if (m <= l - 1) t.fz[i] = s0 * double(l + m) * ratio(l, m, l - 1, m);
             if (m <= l - 3) t.g3[i] = s0 * double(l + m) * ratio(l, m, l - 2, m + 1);
             if (m <= l - 4) t.g2[i] = s0 * ratio(l, m, l - 2, m + 2);
+            const double den = double(l + m + 1) * double(l - m);
+            if (m <= l - 1) t.al[i] = -2.0 * double(m + 1) / den * ratio(l, m, l, m + 1);
+            if (m <= l - 2) t.be[i] = ratio(l, m, l, m + 2) / den;
         }
     }
     return t;

@@ -43,6 +43,8 @@ def test_version_and_limits():
     assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, C.SPH_KERNEL_POINT) == C.SPH_MAX_L_POINT
     assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, C.SPH_KERNEL_SLICE) == C.SPH_MAX_L
     assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_F64, C.SPH_KERNEL_POINT) == -1
+    assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_F64, C.SPH_KERNEL_DEGREE) == C.SPH_MAX_L
+    assert C.sphericart_max_l(C.SPH_F64, C.SPH_Q_NATIVE, C.SPH_KERNEL_DEGREE_DOWN) == C.SPH_MAX_L
 
 
 def _tri(l, m):
@@ -88,6 +90,71 @@ def test_host_recursion_coefficients():
                 assert fz[i] == 0
 
 
+def test_host_downward_coefficients_closed_form():
+    """Folded coefficients of Eq. iter-q-alt (sign-corrected) from the F table
+    ratios vs their closed forms: al = 2(m+1)/sqrt((l+m+1)(l-m)),
+    be = sqrt((l+m+2)(l-m-1)/((l+m+1)(l-m)))."""
+    L = 128
+    al, be = C.sphericart_host_table(L, 7), C.sphericart_host_table(L, 8)
+    for l in range(L + 1):
+        for m in range(l + 1):
+            i = _tri(l, m)
+            want_a = 2 * (m + 1) / math.sqrt((l + m + 1) * (l - m)) if m <= l - 1 else 0.0
+            want_b = math.sqrt((l + m + 2) * (l - m - 1) / ((l + m + 1) * (l - m))) if m <= l - 2 else 0.0
+            assert al[i] == pytest.approx(want_a, rel=1e-12, abs=0), (l, m)
+            assert be[i] == pytest.approx(want_b, rel=1e-12, abs=0), (l, m)
+
+
+def test_host_downward_tables_reproduce_oracle():
+    """The library's downward-in-m tables, run on the host in FP64 (c_m, s_m
+    by Eq. iter-sc, Qtilde_l^m from the tabulated Qtilde_l^l downwards),
+    reproduce the oracle's scaled harmonics (Eq. real-sh-spherical) up to
+    l_max = 40, including points near the poles and on the equator."""
+    L = 40
+    qll, al, be = (C.sphericart_host_table(L, w) for w in (1, 7, 8))
+    rng = np.random.default_rng(3)
+    xyz = rng.normal(size=(64, 3))
+    xyz[:4] = [[1e-5, 2e-5, 1.0], [3e-6, -1e-6, -0.7], [0.6, -0.8, 0.0], [0.0, 0.0, 1.3]]
+    ref = oracle.spherical_harmonics(xyz, L, False)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    rxy2 = x * x + y * y
+    c = [np.ones_like(x)]
+    s = [np.zeros_like(x)]
+    for m in range(1, L + 1):
+        c.append(x * c[-1] - y * s[-1])
+        s.append(x * s[-1] + y * c[-2])
+    got = np.zeros_like(ref)
+    for l in range(L + 1):
+        q1 = np.zeros_like(x)  # Qtilde_l^{m+1}
+        q2 = np.zeros_like(x)  # Qtilde_l^{m+2}
+        for m in range(l, -1, -1):
+            i = _tri(l, m)
+            q = al[i] * z * q1 - be[i] * rxy2 * q2 + (qll[i] if m == l else 0.0)
+            q2, q1 = q1, q
+            if m == 0:
+                got[:, l * l + l] = q / math.sqrt(2)
+            else:
+                got[:, l * l + l + m] = q * c[m]
+                got[:, l * l + l - m] = q * s[m]
+    r = np.linalg.norm(xyz, axis=1)
+    lv = np.concatenate([np.full(2 * l + 1, l) for l in range(L + 1)])
+    err = np.abs(got - ref) / r[:, None] ** lv[None, :]
+    assert err.max() < 1e-12, err.max()
+
+
+def test_auto_family_choice():
+    """AUTO: DEGREE for FP64 arithmetic and for bf16 storage beyond POINT's
+    range, SLICE for FP32 storage beyond it (host-only query)."""
+    fam, shape = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_DEGREE and shape.lanes_per_point in (1, 2, 4)
+    fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_BF16, 1, 0)
+    assert fam == C.SPH_KERNEL_DEGREE
+    fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_SLICE
+    fam, _ = C.sphericart_launch_info(30, C.SPH_F64, C.SPH_OUT_SAME, 1, 1)
+    assert fam == C.SPH_KERNEL_SLICE  # Hessians
+
+
 def _err(fn, *args):
     with pytest.raises(C.SphericartError) as ei:
         fn(*args)
@@ -114,6 +181,11 @@ def test_argument_errors_before_any_cuda_call():
     assert _err(C.sphericart_compute_ex, 16, 4, 17, 0, 0, 0, 0, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 1, 0, 1, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 1, 1, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    # DEGREE families: no Hessians, no backward
+    for k in (C.SPH_KERNEL_DEGREE, C.SPH_KERNEL_DEGREE_DOWN):
+        assert _err(C.sphericart_compute_ex, 16, 4, 30, 0, 0, 0, 0, k, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
+        assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, k, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 5, launch, 16, none, none, none) == C.SPH_EINVAL
     # NULL required pointers
     assert _err(C.sphericart_compute_ex, none, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 0, launch, none, none, none, none) == C.SPH_EINVAL
