@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "hess"],
+        choices=["fwd", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     args = ap.parse_args()
@@ -463,7 +463,7 @@ def run_profile(args):
     n = args.n
     if args.profile in ("fwd", "batch", "hess"):
         L = L_MAX
-    elif args.profile in ("slice20", "degree20"):
+    elif args.profile in ("slice20", "degree20", "row20"):
         L = 20
     else:
         L = BWD_L  # backward kernels and the expansion: l_max = 6
@@ -477,6 +477,8 @@ def run_profile(args):
         fn = lambda: api.spherical_harmonics(x, L, True, gradients=True, kernel="slice")  # noqa: E731
     elif args.profile == "degree20":
         fn = lambda: api.spherical_harmonics(x, L, True, gradients=True, kernel="degree")  # noqa: E731
+    elif args.profile == "row20":
+        fn = lambda: api.spherical_harmonics(x, L, True, gradients=True, kernel="row")  # noqa: E731
     elif args.profile == "hess":
         fn = lambda: api.spherical_harmonics(x, L, gradients=True, hessians=True)  # noqa: E731
     elif args.profile in ("bwd", "dbwd"):

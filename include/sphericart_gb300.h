@@ -78,9 +78,10 @@ typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
 typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
 /* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
- * arithmetic (SPH_F64 or the mixed mode) without Hessians; else POINT when
- * l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else DEGREE for
- * bfloat16 storage without Hessians; else SLICE.
+ * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 12); else
+ * POINT when l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for
+ * FP32 arithmetic without Hessians up to l_max 63; else DEGREE for bfloat16
+ * storage without Hessians; else SLICE.
  *   POINT:  one thread per point, the whole (l, m) recursion unrolled in
  *           registers for a compile-time l_max, outputs staged in shared memory
  *           and written with bulk (TMA) copies.
@@ -94,13 +95,20 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
  *   DEGREE_DOWN: as DEGREE, with Q_l^m of each degree by the downward-in-m
  *           recursion of Eq. iter-q-alt (its printed overall sign corrected:
  *           Q_l^m = -[2(m+1) z Q_l^{m+1} + (x^2+y^2) Q_l^{m+2}]/((l+m+1)(l-m)))
- *           from the tabulated Q_l^l; the paper's one-degree-at-a-time form. */
+ *           from the tabulated Q_l^l; the paper's one-degree-at-a-time form.
+ *   ROW:    FP32 arithmetic, 16 <= l_max <= 63, values and gradients: 8 lanes
+ *           per point (lane j owns the channels m = j mod 8, recursion state in
+ *           registers, degree l uniform across the lanes); each point's output
+ *           rows are staged in shared memory in windows of whole degrees and
+ *           written with TMA bulk copies of 32-byte-aligned runs (~1 KB and
+ *           longer, which GB300's HBM needs for full write bandwidth). */
 typedef enum {
     SPH_KERNEL_AUTO = 0,
     SPH_KERNEL_POINT = 1,
     SPH_KERNEL_SLICE = 2,
     SPH_KERNEL_DEGREE = 3,
-    SPH_KERNEL_DEGREE_DOWN = 4
+    SPH_KERNEL_DEGREE_DOWN = 4,
+    SPH_KERNEL_ROW = 5
 } sph_kernel;
 
 #define SPH_MAX_L 128
@@ -111,8 +119,10 @@ typedef enum {
  *   warps_per_block  independent warps per CTA, 1..8
  *   blocks_per_sm    resident CTAs per SM to size the persistent grid (0 = max)
  *   lanes_per_point  SLICE kernels only: 8, 16 or 32 (0 = by l_max)
- * DEGREE kernels read only warps_per_block (0..8, 0 = by shared memory) and
- * blocks_per_sm; a warp always owns 32 points.                                */
+ * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
+ * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
+ * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
+ * (0..8, 0 = 1) and blocks_per_sm.                                              */
 typedef struct {
     int32_t points_per_tile;
     int32_t warps_per_block;
@@ -137,7 +147,7 @@ int sphericart_compute(const float* xyz, int64_t n, int l_max, int normalized,
  *   qprec  sph_qprec of the Q recursion (SPH_Q_F64 with SPH_F32 only)
  *   kernel sph_kernel family; POINT with l_max > SPH_MAX_L_POINT, with the
  *          mixed mode or with bfloat16 Hessians returns SPH_EUNSUPPORTED, and
- *          so do the DEGREE families with ddsph
+ *          so do the DEGREE families with ddsph and ROW outside its range
  *   launch NULL or a launch shape (zeros = default)
  * SPH_EUNSUPPORTED also for BF16 output with FP64 arithmetic. */
 int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,

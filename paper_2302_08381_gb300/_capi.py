@@ -17,7 +17,8 @@ SPH_OK, SPH_EINVAL, SPH_EUNSUPPORTED, SPH_ECUDA, SPH_ENOMEM, SPH_ETIMEOUT = rang
 SPH_F32, SPH_F64 = 0, 1
 SPH_OUT_SAME, SPH_OUT_BF16 = 0, 1
 SPH_Q_NATIVE, SPH_Q_F64 = 0, 1
-SPH_KERNEL_AUTO, SPH_KERNEL_POINT, SPH_KERNEL_SLICE, SPH_KERNEL_DEGREE, SPH_KERNEL_DEGREE_DOWN = 0, 1, 2, 3, 4
+SPH_KERNEL_AUTO, SPH_KERNEL_POINT, SPH_KERNEL_SLICE, SPH_KERNEL_DEGREE, SPH_KERNEL_DEGREE_DOWN, SPH_KERNEL_ROW = (
+    0, 1, 2, 3, 4, 5)
 SPH_MAX_L = 128
 SPH_MAX_L_POINT = 16
 

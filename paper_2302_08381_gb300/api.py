@@ -15,6 +15,7 @@ _KERNELS = {
     "slice": C.SPH_KERNEL_SLICE,
     "degree": C.SPH_KERNEL_DEGREE,
     "degree_down": C.SPH_KERNEL_DEGREE_DOWN,
+    "row": C.SPH_KERNEL_ROW,
 }
 _QPREC = {"native": C.SPH_Q_NATIVE, "f64": C.SPH_Q_F64}
 

@@ -289,21 +289,23 @@ bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % 
 // (measured on GB300: FP64 prefers 2 lanes per point up to l_max ~ 24 and 4
 // above, FP32 arithmetic with FP64 Q ("mixed") 2, FP32 / bf16 storage 4).
 int degree_default_lpp(int l_max, int dtype, int qprec) {
-    if (dtype == SPH_F64) return l_max >= 24 ? 4 : 2;
+    if (dtype == SPH_F64) return l_max >= 24 ? 4 : (l_max >= 12 ? 2 : 1);
     if (qprec == SPH_Q_F64) return 2;
     return 4;
 }
 
-// AUTO kernel family of a forward request. POINT (compile-time l_max, TMA
-// bulk stores) wins whenever it applies in FP32; FP64 arithmetic (FP64 inputs
-// or the mixed mode) is bound by GB300's FP64 pipe, where the DEGREE family
-// (no idle lanes) is fastest at every measured l_max; beyond POINT's range,
-// bf16 storage is fastest on DEGREE and FP32 storage on SLICE; Hessians stay
-// on POINT / SLICE.
+// AUTO kernel family of a forward request (measured on GB300). POINT
+// (compile-time l_max, TMA bulk stores) wins whenever it applies in FP32, and
+// in FP64 up to l_max ~ 10; beyond that FP64 arithmetic (FP64 inputs or the
+// mixed mode) is bound by GB300's FP64 pipe, where the DEGREE family (no idle
+// lanes) is fastest; beyond POINT's range FP32 arithmetic runs on ROW up to
+// its l_max 63 (1.8-2.2x SLICE), then on SLICE (DEGREE for bf16 storage);
+// Hessians stay on POINT / SLICE.
 int auto_family(int l_max, int dtype, int out, int qprec, bool hess) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
-    if (!hess && (dtype == SPH_F64 || mixed)) return SPH_KERNEL_DEGREE;
+    if (!hess && (mixed || (dtype == SPH_F64 && l_max >= 12))) return SPH_KERNEL_DEGREE;
     if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
+    if (!hess && dtype == SPH_F32 && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && out == SPH_OUT_BF16) return SPH_KERNEL_DEGREE;
     return SPH_KERNEL_SLICE;
 }
@@ -329,7 +331,7 @@ int check_common(int64_t n, int l_max, int dtype, int kernel) {
         return SPH_EINVAL;
     }
     if (kernel != SPH_KERNEL_AUTO && kernel != SPH_KERNEL_POINT && kernel != SPH_KERNEL_SLICE &&
-        kernel != SPH_KERNEL_DEGREE && kernel != SPH_KERNEL_DEGREE_DOWN) {
+        kernel != SPH_KERNEL_DEGREE && kernel != SPH_KERNEL_DEGREE_DOWN && kernel != SPH_KERNEL_ROW) {
         set_error("kernel=%d is not an sph_kernel", kernel);
         return SPH_EINVAL;
     }
@@ -361,6 +363,7 @@ const char* sphericart_last_error(void) { return last_error_message(); }
 
 int sphericart_max_l(int dtype, int qprec, int kernel) {
     if (kernel == SPH_KERNEL_POINT) return (qprec == SPH_Q_F64 && dtype == SPH_F32) ? -1 : SPH_MAX_L_POINT;
+    if (kernel == SPH_KERNEL_ROW) return (dtype == SPH_F32 && qprec == SPH_Q_NATIVE) ? kRowMaxL : -1;
     (void)dtype;
     return SPH_MAX_L;
 }
@@ -404,6 +407,11 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     if (fam == SPH_KERNEL_AUTO) fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr);
     if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || hess_bf16 || mixed)) {
         set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
+        return SPH_EUNSUPPORTED;
+    }
+    if (fam == SPH_KERNEL_ROW && (ddsph || mixed || dtype != SPH_F32 || l_max < kRowMinL || l_max > kRowMaxL)) {
+        set_error("ROW kernels take FP32 arithmetic, %d <= l_max <= %d, values and gradients only", kRowMinL,
+                  kRowMaxL);
         return SPH_EUNSUPPORTED;
     }
     const bool degree = fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN;
@@ -474,6 +482,19 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
         }
         return cuda_status(e, "DEGREE forward launch");
     }
+    if (fam == SPH_KERNEL_ROW) {
+        if (a.launch.warps_per_block < 0 || a.launch.warps_per_block > 8 || a.launch.blocks_per_sm < 0 ||
+            a.launch.blocks_per_sm > 32) {
+            set_error("ROW launch: warps_per_block must be in [0,8] and blocks_per_sm in [0,32]");
+            return SPH_EINVAL;
+        }
+        const int e = (l_max + 1 + 7) / 8 <= 5 ? row_fwd_part0(a) : row_fwd_part1(a);
+        if (e == int(cudaErrorInvalidConfiguration)) {
+            set_error("ROW launch shape needs more shared memory per block than the device allows");
+            return SPH_EINVAL;
+        }
+        return cuda_status(e, "ROW forward launch");
+    }
     if (!valid_lanes(a.launch)) return SPH_EINVAL;
     return cuda_status(slice_fwd(a), "SLICE forward launch");
 }
@@ -494,7 +515,7 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
         set_error("POINT kernels take l_max <= %d", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
-    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN) {
+    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN || fam == SPH_KERNEL_ROW) {
         set_error("backward passes run on the POINT or SLICE kernels");
         return SPH_EUNSUPPORTED;
     }
@@ -576,6 +597,9 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
     if (fam == SPH_KERNEL_DEGREE) {
         *kernel_out = SPH_KERNEL_DEGREE;
         *launch_out = sph_launch{0, 0, 0, degree_default_lpp(l_max, dtype, SPH_Q_NATIVE)};
+    } else if (fam == SPH_KERNEL_ROW) {
+        *kernel_out = SPH_KERNEL_ROW;
+        *launch_out = sph_launch{0, 1, 0, 8};
     } else if (fam == SPH_KERNEL_POINT) {
         *kernel_out = SPH_KERNEL_POINT;
         sph_launch s{0, 0, 0, 0};

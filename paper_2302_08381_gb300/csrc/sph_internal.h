@@ -126,6 +126,13 @@ int degree_fwd_up2(const FwdArgs& a);
 int degree_fwd_up4(const FwdArgs& a);
 int degree_fwd_down(const FwdArgs& a);
 
+// ROW kernels (FP32 arithmetic, 16 <= l_max <= 63, values and gradients):
+// part 0 covers 3..5 channels per lane (l_max <= 47), part 1 6..8.
+int row_fwd_part0(const FwdArgs& a);
+int row_fwd_part1(const FwdArgs& a);
+constexpr int kRowMinL = 16;
+constexpr int kRowMaxL = 63;
+
 // SLICE kernels (runtime l_max).
 int slice_fwd(const FwdArgs& a);
 int slice_bwd(const BwdArgs& a);

@@ -1,0 +1,362 @@
+// ROW kernel family: FP32 forward (values, gradients) for 16 <= l_max <= 63
+// whose global writes are long contiguous runs.
+//
+// On GB300 the write stream reaches the HBM roofline only in contiguous runs
+// of about 1 KB or more (measured: scattered 128-byte runs reach ~0.8 TB/s,
+// 512-byte runs ~3.2 TB/s, >= 1 KB runs ~6.2 TB/s). A kernel that writes one
+// degree (2l+1 columns) of many output rows at a time cannot get there, so
+// this family keeps each point's output rows in shared memory in windows of
+// whole degrees (about 130..250 columns per plane) and sends every window
+// with TMA bulk copies of 32-byte-aligned runs.
+//
+// Work decomposition (arXiv 2302.08381, Section 2): a group of 8 lanes owns a
+// point, a warp owns 4 consecutive points. The degree l is the outer loop and
+// is the same for the whole group; lane j owns the m channels m = j (mod 8),
+// whose Qtilde_{l-1}^m, Qtilde_{l-2}^m (Eq. iter-q with the prefactors folded
+// in, Appendix C) and c_m, s_m, c_{m-1}, s_{m-1} (Eq. iter-sc) stay in
+// registers; the derivative identities of Eq. iter-deri need
+// Qtilde_{l-1}^{m+1}, which the neighbouring lane holds and passes with a
+// shuffle. At every degree the lanes of a group write 8 consecutive columns
+// per side, so the shared-memory stores are conflict-free within a group.
+//
+// The translation unit is compiled twice: SPH_ROW_PART 0 instantiates the
+// kernels for 3..5 channels per lane (l_max 16..47), 1 for 6..8 (48..63).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sph_core.cuh"
+#include "sph_internal.h"
+
+#ifndef SPH_ROW_PART
+#define SPH_ROW_PART 0
+#endif
+
+namespace sph {
+
+namespace {
+
+constexpr int kG = 8;         // lanes per point
+constexpr int kPW = 32 / kG;  // points per warp
+constexpr int kCap = 256;     // columns a plane buffer holds after its pre-slots
+
+// Per output type: elements per 32-byte sector, the plane buffer length (SE
+// pre-slots for the row head, then kCap columns; a multiple of 16 bytes), and
+// the distance between the buffers of consecutive points, which is 8 four-byte
+// words past a multiple of 32 so that the four point groups of a warp, each
+// writing 8 consecutive columns, start 8 banks apart.
+template <typename TO>
+struct RowGeom {
+    static constexpr int SE = 32 / int(sizeof(TO));
+    static constexpr int BUF = SE + kCap;
+    template <int NPL>
+    __host__ __device__ static constexpr int point_stride() {
+        constexpr int words = NPL * BUF * int(sizeof(TO)) / 4;
+        constexpr int pad = ((8 - words % 32) + 32) % 32;  // words of padding
+        return NPL * BUF + pad * 4 / int(sizeof(TO));
+    }
+};
+
+template <typename TO, bool GRAD>
+__host__ __device__ constexpr size_t row_warp_bytes() {
+    return size_t(kPW) * RowGeom<TO>::template point_stride<GRAD ? 4 : 1>() * sizeof(TO);
+}
+
+struct CSf {
+    float c, s;
+    __device__ __forceinline__ CSf times(const CSf& w) const {
+        return CSf{fmaf(c, w.c, -(s * w.s)), fmaf(c, w.s, s * w.c)};
+    }
+};
+
+template <typename TO, bool GRAD, bool NORM, int NCH>
+__global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ xyz, int64_t n, int L,
+                                                      const float* __restrict__ tb, float inv_sqrt2,
+                                                      TO* __restrict__ sph, TO* __restrict__ dsph) {
+    constexpr int NPL = GRAD ? 4 : 1;
+    constexpr int SE = RowGeom<TO>::SE;
+    constexpr int BUF = RowGeom<TO>::BUF;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int g = lane / kG;  // point of the warp tile
+    const int j = lane % kG;  // channel class m = j (mod 8)
+    constexpr int PSTR = RowGeom<TO>::template point_stride<NPL>();
+    TO* const pst = reinterpret_cast<TO*>(smem) + (size_t(warp) * kPW + g) * PSTR;  // this point's planes
+    const int64_t K = int64_t(L + 1) * (L + 1);
+    const int64_t ntiles = (n + kPW - 1) / kPW;
+    const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tb);
+    const int nb_lane = (lane & ~(kG - 1)) | ((j + 1) & (kG - 1));  // the lane holding channel m+1's class
+
+    for (int64_t tile = int64_t(blockIdx.x) * W + warp; tile < ntiles; tile += int64_t(gridDim.x) * W) {
+        const int64_t p = tile * kPW + g;
+        const bool live = p < n;
+        float x = 0.f, y = 0.f, z = 0.f, ir = 1.f;
+        if (live) {
+            x = xyz[3 * p];
+            y = xyz[3 * p + 1];
+            z = xyz[3 * p + 2];
+        }
+        if (NORM) {
+            const float rr = fmaf(x, x, fmaf(y, y, z * z));
+            ir = rr > 0.f ? 1.f / sqrtf(rr) : 0.f;
+            x *= ir;
+            y *= ir;
+            z *= ir;
+        }
+        const float r2 = fmaf(z, z, fmaf(x, x, y * y));
+
+        // c_m + i s_m and c_{m-1} + i s_{m-1} of the lane's channels m = j + 8k.
+        float cm[NCH], sm[NCH], cm1[NCH], sm1[NCH];
+        {
+            const CSf xy{x, y};
+            CSf a{1.f, 0.f}, b{1.f, 0.f}, w8{1.f, 0.f}, p7{1.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < kG; ++t) {
+                if (t < j) a = a.times(xy);
+                if (t < j - 1) b = b.times(xy);
+                if (t < kG - 1) p7 = p7.times(xy);
+                w8 = w8.times(xy);
+            }
+            if (j == 0) b = p7;  // channel 8k (k >= 1) needs (x + i y)^(8k-1)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                cm[k] = a.c;
+                sm[k] = a.s;
+                const bool none = (j == 0 && k == 0);  // m = 0 has no c_{m-1}
+                cm1[k] = none ? 0.f : b.c;
+                sm1[k] = none ? 0.f : b.s;
+                a = a.times(w8);
+                if (!none) b = b.times(w8);
+            }
+        }
+        float q1[NCH], q2[NCH];  // Qtilde_{l-1}^m, Qtilde_{l-2}^m
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) q1[k] = q2[k] = 0.f;
+
+        // Output rows of this point: plane 0 = sph row, planes 1..3 = dsph rows.
+        // s[i] = first column held in the plane buffer (at slot SE); it is
+        // 32-byte aligned in global memory, so every bulk copy starts and
+        // (except at the row end) ends on a sector boundary.
+        TO* grow[NPL];
+        int s[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            grow[i] = (i == 0) ? sph + p * K : dsph + p * 3 * K + (i - 1) * K;
+            const int phase = int((reinterpret_cast<uintptr_t>(grow[i]) / sizeof(TO)) % SE);
+            s[i] = (SE - phase) % SE;
+        }
+
+        // Coefficients of degree d for the lane's channels (clamped to a valid
+        // entry where m > d), loaded one degree ahead.
+        float4 ta[NCH];
+        float tf[NCH];
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+            const int i = tri(0, 0);
+            ta[k] = t4[2 * i];
+            tf[k] = tb[8 * i + 4];
+        }
+
+        int l = 0;
+        bool first = true;
+        while (l <= L) {
+            // A window of whole degrees [l, lw): columns [l^2, lw^2).
+            int lw = l + 1;
+            while (lw <= L && (lw + 1) * (lw + 1) - l * l <= kCap - (SE - 1)) ++lw;
+            for (int d = l; d < lw; ++d) {
+                const int ctr = d * d + d;
+                const int kend = d / kG;  // channels m = j + 8k <= d need k <= d/8 (same for the whole warp)
+                float4 na[NCH];
+                float nf[NCH];
+                {
+                    const int dn = d < L ? d + 1 : L;
+#pragma unroll
+                    for (int k = 0; k < NCH; ++k) {
+                        const int mk = j + kG * k;
+                        const int i = tri(dn, mk <= dn ? mk : dn);
+                        na[k] = t4[2 * i];
+                        nf[k] = GRAD ? tb[8 * i + 4] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    if (k > kend) break;
+                    const int m = j + kG * k;
+                    const bool on = m <= d;
+                    const float4 t0 = ta[k];  // {A, B, S, e}
+                    const float src = (j == 0) ? (k + 1 < NCH ? q1[k + 1 < NCH ? k + 1 : k] : 0.f) : q1[k];
+                    const float qn = __shfl_sync(0xffffffffu, src, nb_lane);  // Qtilde_{l-1}^{m+1}
+                    float q = fmaf(t0.x * z, q1[k], fmaf(-(t0.y * r2), q2[k], t0.z));
+                    q = on ? q : 0.f;
+                    if (on) {
+                        QParts<float> qp;
+                        qp.Q = q;
+                        qp.G2 = qp.G3 = qp.G4 = 0.f;
+                        if (GRAD) {
+                            qp.E1 = t0.w * qn;
+                            qp.Qz = tf[k] * q1[k];
+                        } else {
+                            qp.E1 = qp.Qz = 0.f;
+                        }
+                        if (m == 0) {
+                            Deriv<float> dd = assemble_m0<GRAD, false>(qp, x, y, inv_sqrt2);
+                            if (NORM && GRAD) normalize_deriv<false>(dd, d, x, y, z, ir);
+                            pst[ctr - s[0] + SE] = OutConv<TO>::cv(dd.v);
+                            if (GRAD) {
+                                pst[BUF + ctr - s[1 % NPL] + SE] = OutConv<TO>::cv(dd.gx);
+                                pst[2 * BUF + ctr - s[2 % NPL] + SE] = OutConv<TO>::cv(dd.gy);
+                                pst[3 * BUF + ctr - s[3 % NPL] + SE] = OutConv<TO>::cv(dd.gz);
+                            }
+                        } else {
+                            Deriv<float> dc, ds;
+                            assemble_m<GRAD, false>(qp, x, y, float(m), float(m - 1), cm[k], sm[k], cm1[k], sm1[k],
+                                                    0.f, 0.f, dc, ds);
+                            if (NORM && GRAD) {
+                                normalize_deriv<false>(dc, d, x, y, z, ir);
+                                normalize_deriv<false>(ds, d, x, y, z, ir);
+                            }
+                            const int cp = ctr + m, cn = ctr - m;
+                            pst[cp - s[0] + SE] = OutConv<TO>::cv(dc.v);
+                            pst[cn - s[0] + SE] = OutConv<TO>::cv(ds.v);
+                            if (GRAD) {
+                                pst[BUF + cp - s[1 % NPL] + SE] = OutConv<TO>::cv(dc.gx);
+                                pst[BUF + cn - s[1 % NPL] + SE] = OutConv<TO>::cv(ds.gx);
+                                pst[2 * BUF + cp - s[2 % NPL] + SE] = OutConv<TO>::cv(dc.gy);
+                                pst[2 * BUF + cn - s[2 % NPL] + SE] = OutConv<TO>::cv(ds.gy);
+                                pst[3 * BUF + cp - s[3 % NPL] + SE] = OutConv<TO>::cv(dc.gz);
+                                pst[3 * BUF + cn - s[3 % NPL] + SE] = OutConv<TO>::cv(ds.gz);
+                            }
+                        }
+                    }
+                    q2[k] = q1[k];
+                    q1[k] = q;
+                }
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    ta[k] = na[k];
+                    tf[k] = nf[k];
+                }
+            }
+
+            // Send the window: per plane, the sector-aligned run [s, e) by one
+            // bulk copy; the row head (first window) and the row tail (last
+            // window) with plain stores; the rest (< one sector) is carried.
+            const int c_hi = lw * lw;
+            const bool last = lw > L;
+            fence_proxy_async_smem();
+            __syncwarp();
+            int e[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int run = last ? (c_hi - s[i]) * int(sizeof(TO)) / 16 * 16 / int(sizeof(TO))
+                                     : (c_hi - s[i]) / SE * SE;
+                e[i] = s[i] + max(run, 0);
+            }
+            if (live) {
+                if (j == 0) {
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i)
+                        if (e[i] > s[i])
+                            bulk_store(grow[i] + s[i], pst + i * BUF + SE, uint32_t((e[i] - s[i]) * sizeof(TO)));
+                    bulk_commit();
+                }
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    for (int c = j; first && c < s[i]; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
+                    for (int c = e[i] + j; last && c < c_hi; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
+                }
+                if (j == 0) bulk_wait_read_all();  // the buffers are reused below
+            }
+            __syncwarp();
+            if (!last) {
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    for (int c = e[i] + j; c < c_hi; c += kG) pst[i * BUF + c - e[i] + SE] = pst[i * BUF + c - s[i] + SE];
+                    s[i] = e[i];
+                }
+                __syncwarp();
+            }
+            first = false;
+            l = lw;
+        }
+    }
+    if (j == 0) bulk_wait_all();
+}
+
+template <typename TO, bool GRAD, bool NORM, int NCH>
+int launch_row(const FwdArgs& a, const float* tb) {
+    auto kern = row_fwd_kernel<TO, GRAD, NORM, NCH>;
+    const size_t per_warp = row_warp_bytes<TO, GRAD>();
+    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : 1;  // measured: 1 >= 2 > 4 > 8
+    const size_t smem = size_t(W) * per_warp;
+    if (smem > size_t(max_smem_optin())) return int(cudaErrorInvalidConfiguration);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return int(e);
+    }
+    int bps = a.launch.blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), 32 * W, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        bps = std::max(occ, 1);
+    }
+    const int64_t ntiles = (a.n + kPW - 1) / kPW;
+    const int64_t want = (ntiles + W - 1) / W;
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const float*>(a.xyz), a.n, a.l_max, tb, float(host_tables().inv_sqrt2), static_cast<TO*>(a.sph),
+        static_cast<TO*>(a.dsph));
+    return int(cudaGetLastError());
+}
+
+template <typename TO, int NCH>
+int launch_row_flags(const FwdArgs& a, const float* tb) {
+    const bool grad = a.dsph != nullptr, norm = a.normalized != 0;
+    if (grad) return norm ? launch_row<TO, true, true, NCH>(a, tb) : launch_row<TO, true, false, NCH>(a, tb);
+    return norm ? launch_row<TO, false, true, NCH>(a, tb) : launch_row<TO, false, false, NCH>(a, tb);
+}
+
+template <int NCH>
+int launch_row_out(const FwdArgs& a, const float* tb) {
+    if (a.out == SPH_OUT_BF16) return launch_row_flags<__nv_bfloat16, NCH>(a, tb);
+    return launch_row_flags<float, NCH>(a, tb);
+}
+
+}  // namespace
+
+#if SPH_ROW_PART == 0
+int row_fwd_part0(const FwdArgs& a) {
+    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
+    if (!tb) return int(cudaErrorMemoryAllocation);
+    switch ((a.l_max + 1 + kG - 1) / kG) {
+        case 3:
+            return launch_row_out<3>(a, tb);
+        case 4:
+            return launch_row_out<4>(a, tb);
+        default:
+            return launch_row_out<5>(a, tb);
+    }
+}
+#else
+int row_fwd_part1(const FwdArgs& a) {
+    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
+    if (!tb) return int(cudaErrorMemoryAllocation);
+    switch ((a.l_max + 1 + kG - 1) / kG) {
+        case 6:
+            return launch_row_out<6>(a, tb);
+        case 7:
+            return launch_row_out<7>(a, tb);
+        default:
+            return launch_row_out<8>(a, tb);
+    }
+}
+#endif
+
+}  // namespace sph

@@ -143,14 +143,19 @@ def test_host_downward_tables_reproduce_oracle():
 
 
 def test_auto_family_choice():
-    """AUTO: DEGREE for FP64 arithmetic and for bf16 storage beyond POINT's
-    range, SLICE for FP32 storage beyond it (host-only query)."""
-    fam, shape = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
+    """AUTO: DEGREE for FP64 arithmetic from l_max 12; ROW for FP32
+    arithmetic from POINT's range to l_max 63; then SLICE (FP32 storage) or
+    DEGREE (bf16 storage); Hessians on SLICE (host-only query)."""
+    fam, shape = C.sphericart_launch_info(16, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
     assert fam == C.SPH_KERNEL_DEGREE and shape.lanes_per_point in (1, 2, 4)
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_BF16, 1, 0)
-    assert fam == C.SPH_KERNEL_DEGREE
+    assert fam == C.SPH_KERNEL_ROW
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_ROW
+    fam, _ = C.sphericart_launch_info(64, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
     assert fam == C.SPH_KERNEL_SLICE
+    fam, _ = C.sphericart_launch_info(64, C.SPH_F32, C.SPH_OUT_BF16, 1, 0)
+    assert fam == C.SPH_KERNEL_DEGREE
     fam, _ = C.sphericart_launch_info(30, C.SPH_F64, C.SPH_OUT_SAME, 1, 1)
     assert fam == C.SPH_KERNEL_SLICE  # Hessians
 
@@ -185,7 +190,16 @@ def test_argument_errors_before_any_cuda_call():
     for k in (C.SPH_KERNEL_DEGREE, C.SPH_KERNEL_DEGREE_DOWN):
         assert _err(C.sphericart_compute_ex, 16, 4, 30, 0, 0, 0, 0, k, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
         assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, k, launch, 16, none) == C.SPH_EUNSUPPORTED
-    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 5, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 6, launch, 16, none, none, none) == C.SPH_EINVAL
+    # ROW: FP32 arithmetic, 16 <= l_max <= 63, no Hessians, no backward
+    R = C.SPH_KERNEL_ROW
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 64, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 1, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 1, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 0, R, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, R, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, R) == 63
     # NULL required pointers
     assert _err(C.sphericart_compute_ex, none, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 0, launch, none, none, none, none) == C.SPH_EINVAL

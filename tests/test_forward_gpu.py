@@ -205,11 +205,12 @@ def test_outputs_do_not_overrun():
 
 
 # --------------------------------------------------------------- large l_max, precision
+@pytest.mark.parametrize("kernel", ["auto", "slice"])
 @pytest.mark.parametrize("l_max", [17, 20, 31, 33])
-def test_slice_large_lmax_f32(l_max):
+def test_slice_large_lmax_f32(l_max, kernel):
     xyz = inputs.shell_points(500, 0.7, 1.3, seed=107).astype(np.float64)
     x32 = xyz.astype(np.float32).astype(np.float64)
-    v, g = _run(x32, l_max, False, True, "auto")
+    v, g = _run(x32, l_max, False, True, kernel)
     rv, rg = oracle.spherical_harmonics_grad(x32, l_max, False)
     ev = value_errors(v, rv, x32, l_max, False)
     eg = grad_errors(g, rg, x32, l_max, False)
