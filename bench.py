@@ -616,12 +616,23 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (100_000, 8, "l8_values_f32_n100k", dict(), 4, 1),
         (100_000, 8, "l8_grad_f32_n100k", dict(gradients=True), 4, 4),
         (100_000, 8, "l8_grad_f64_n100k", dict(gradients=True), 8, 4),
-        # the high-degree precision-sweep sizes (SLICE kernels), normalized
+        # the high-degree precision-sweep sizes, normalized (AUTO: ROW for FP32
+        # arithmetic, DEGREE for FP64 arithmetic), and the other families
         (200_000, 20, "l20_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
         (200_000, 30, "l30_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
         (200_000, 50, "l50_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
+        (200_000, 63, "l63_grad_f32_norm_n200k", dict(gradients=True, normalized=True), 4, 4),
+        (200_000, 20, "l20_grad_f32_norm_n200k_slice", dict(gradients=True, normalized=True, kernel="slice"), 4, 4),
+        (200_000, 50, "l50_grad_f32_norm_n200k_slice", dict(gradients=True, normalized=True, kernel="slice"), 4, 4),
+        (200_000, 20, "l20_grad_f32_norm_n200k_degree", dict(gradients=True, normalized=True, kernel="degree"), 4, 4),
+        (200_000, 20, "l20_grad_bf16_norm_n200k", dict(gradients=True, normalized=True, out_dtype=torch.bfloat16), 2, 4),
+        (1_000_000, 20, "l20_grad_f32_n1M", dict(gradients=True), 4, 4),
         (200_000, 50, "l50_grad_mixed_norm_n200k", dict(gradients=True, normalized=True, qprec="f64"), 4, 4),
         (200_000, 50, "l50_grad_f64_norm_n200k", dict(gradients=True, normalized=True), 8, 4),
+        (200_000, 50, "l50_grad_f64_norm_n200k_slice", dict(gradients=True, normalized=True, kernel="slice"), 8, 4),
+        (200_000, 50, "l50_grad_f64_norm_n200k_degree_down",
+         dict(gradients=True, normalized=True, kernel="degree_down"), 8, 4),
+        (1_000_000, 16, "l16_grad_f64_n1M", dict(gradients=True), 8, 4),
     ):
         dt = torch.float64 if elem == 8 else torch.float32
         x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)
@@ -632,8 +643,10 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
 
         # POINT-family forward variants use the library's autotuner too (as the
         # headline does); value-only / gradient / bf16 / FP64 shapes are tuned
-        # separately, Hessian shapes keep their defaults.
-        if L <= 16 and "kernel" not in kw and "qprec" not in kw and not kw.get("hessians"):
+        # separately, Hessian shapes keep their defaults; the other families
+        # take their default shapes.
+        auto_point = L <= 16 if dt == torch.float32 else L <= 11  # where AUTO runs the POINT kernels
+        if auto_point and "kernel" not in kw and "qprec" not in kw and not kw.get("hessians"):
             from paper_2302_08381_gb300 import _capi as C
 
             sph = torch.empty((n, K), dtype=kw.get("out_dtype", dt) or dt, device=dev)
@@ -709,15 +722,19 @@ def run_e2e(torch, api, inputs, dev, n, L, K, seed):
         api.spherical_harmonics_host(xyz_h, L, False, gradients=True, out=(sph_h, dsph_h), workspace=ws,
                                      chunk_points=chunk, device=dev)
 
-    for _ in range(2):
+    # The first transfers into freshly pinned buffers (and the first after a
+    # CPU write to them) run several times slower on this machine: 3 warm-up
+    # steps, then the median of 7 synchronised steps.
+    for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
-    reps = 5
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    times = []
+    for _ in range(7):
+        t0 = time.perf_counter()
         e2e_step()
-    torch.cuda.synchronize()
-    return (time.perf_counter() - t0) / reps
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times)
 
 
 def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
