@@ -529,9 +529,9 @@ def _events_ms(torch, stream, fn, reps, flush=None):
 
 def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
     """512 ragged sets (sizes log-uniform in [1e3, 2e5], l_max from {3,6,8,12},
-    N(0,1) FP32 points), values + gradients: one persistent launch (eager and
-    replayed from a CUDA graph) vs one launch per set (eager and captured in
-    one graph)."""
+    N(0,1) FP32 points), values + gradients: the plan's persistent launches
+    (one per l_max class, and one for all sets; eager and replayed from a CUDA
+    graph) vs one launch per set (eager and captured in one graph)."""
     sizes, lmax, xyz = inputs.ragged_sets(512, [3, 6, 8, 12], 1000, 200_000, seed=5)
     offs = np.concatenate([[0], np.cumsum(sizes)])
     xt = torch.from_numpy(xyz).to(dev)
@@ -552,22 +552,27 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
     C.check("sphericart_batch_autotune", C.lib().sphericart_batch_autotune(
         arr, len(xs), stream.cuda_stream, 2, ctypes.byref(best), ctypes.byref(best_ms)))
     plan.close()
-    plan = api.BatchPlan(xs, ls, launch=best, outputs=outs)
+    plan = api.BatchPlan(xs, ls, launch=best, outputs=outs)  # one persistent launch per l_max class
+    one = api.BatchPlan(xs, ls, launch=best, outputs=outs, mode="one_launch")
 
     def per_set():
         for x, L, o in zip(xs, ls, outs):
             api.spherical_harmonics(x, L, gradients=True, out=o)
 
     plan.execute()
+    one.execute()
     per_set()
     torch.cuda.synchronize()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     g_plan = torch.cuda.CUDAGraph()
+    g_one = torch.cuda.CUDAGraph()
     g_sets = torch.cuda.CUDAGraph()
     with torch.cuda.stream(side):
         with torch.cuda.graph(g_plan, stream=side):
             plan.execute()
+        with torch.cuda.graph(g_one, stream=side):
+            one.execute()
         with torch.cuda.graph(g_sets, stream=side):
             per_set()
     stream.wait_stream(side)
@@ -582,8 +587,10 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
         "algorithmic_bytes": nbytes,
     }
     for name, fn in (
-        ("persistent_launch", plan.execute),
-        ("persistent_graph", g_plan.replay),
+        ("persistent_per_lmax", plan.execute),
+        ("persistent_per_lmax_graph", g_plan.replay),
+        ("persistent_one_launch", one.execute),
+        ("persistent_one_launch_graph", g_one.replay),
         ("per_set_launches", per_set),
         ("per_set_graph", g_sets.replay),
     ):
@@ -594,6 +601,7 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
         res[name + "_points_per_s"] = total / (ms * 1e-3)
         res[name + "_GBs"] = nbytes / (ms * 1e-3) / 1e9
     plan.close()
+    one.close()
     return res
 
 

@@ -232,8 +232,9 @@ typedef struct {
 typedef struct sph_batch_plan sph_batch_plan;
 
 /* sphericart_batch_plan_create: builds the device work list for `nsets` sets
- * (copied from host memory) for ONE persistent launch in which every warp pulls
- * tiles from a device counter and branches on the set's l_max. The plan owns
+ * (copied from host memory) for persistent launches in which every warp pulls
+ * tiles from a device counter: one launch per distinct l_max (mode
+ * SPH_BATCH_PER_LMAX, see sphericart_batch_plan_create_ex). The plan owns
  * its device work list (allocated here, freed by _destroy). Buffers of the sets
  * must stay valid while the plan is executed. `launch` may be NULL (default
  * shape); points_per_tile is chosen per l_max to fit a fixed shared-memory
@@ -242,8 +243,25 @@ typedef struct sph_batch_plan sph_batch_plan;
 int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets,
                                  const sph_launch* launch, sph_batch_plan** plan);
 
-/* sphericart_batch_execute: enqueues the persistent launch (counter reset +
- * kernel) on `stream`. Capturable in a CUDA graph. */
+/* How a plan runs its sets:
+ *   SPH_BATCH_PER_LMAX   one persistent launch per distinct l_max, each compiled
+ *                        for that l_max alone, with its own tile counter and a
+ *                        shared-memory size fitted to that l_max's tile (the
+ *                        default of sphericart_batch_plan_create; measured faster
+ *                        on GB300)
+ *   SPH_BATCH_ONE_LAUNCH one persistent launch for every set, branching on each
+ *                        tile's l_max, shared memory sized for the largest tile */
+typedef enum { SPH_BATCH_PER_LMAX = 0, SPH_BATCH_ONE_LAUNCH = 1 } sph_batch_mode;
+
+/* sphericart_batch_plan_create_ex: sphericart_batch_plan_create with a mode
+ * (sph_batch_mode; SPH_EINVAL for any other value). */
+int sphericart_batch_plan_create_ex(const sph_batch_set* sets, int nsets,
+                                    const sph_launch* launch, int mode,
+                                    sph_batch_plan** plan);
+
+/* sphericart_batch_execute: enqueues the plan's launches (one counter reset,
+ * then one persistent kernel per launch) on `stream`. Capturable in a CUDA
+ * graph. */
 int sphericart_batch_execute(const sph_batch_plan* plan, void* stream);
 
 /* sphericart_batch_plan_destroy: frees the plan (synchronises its device). */
@@ -332,7 +350,9 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized,
  * per-warp shared-memory budgets, warps per block and blocks per SM, and
  * returns the fastest shape for sphericart_batch_plan_create (for batch plans
  * points_per_tile, 0..160, sets the per-warp budget as that many l_max = 8
- * FP32 value+gradient rows of 1296 bytes; 0 = 32 rows).
+ * FP32 value+gradient rows of 1296 bytes; 0 = 32 rows; with points_per_tile
+ * and warps_per_block both 0 a SPH_BATCH_PER_LMAX plan gives every l_max class
+ * the single-set POINT kernel's tile and warps per block for that l_max).
  * Overwrites the sets' outputs; synchronises. */
 int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream,
                               int reps, sph_launch* best, float* best_ms);

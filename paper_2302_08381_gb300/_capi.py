@@ -19,6 +19,7 @@ SPH_OUT_SAME, SPH_OUT_BF16 = 0, 1
 SPH_Q_NATIVE, SPH_Q_F64 = 0, 1
 SPH_KERNEL_AUTO, SPH_KERNEL_POINT, SPH_KERNEL_SLICE, SPH_KERNEL_DEGREE, SPH_KERNEL_DEGREE_DOWN, SPH_KERNEL_ROW = (
     0, 1, 2, 3, 4, 5)
+SPH_BATCH_PER_LMAX, SPH_BATCH_ONE_LAUNCH = 0, 1
 SPH_MAX_L = 128
 SPH_MAX_L_POINT = 16
 
@@ -73,6 +74,8 @@ _PROTOS = {
     ),
     "sphericart_expansion": (_I, [_P, _P, _P, _I64, _I64, _I, _I, _I, _I, _P, _P]),
     "sphericart_batch_plan_create": (_I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), ctypes.POINTER(_P)]),
+    "sphericart_batch_plan_create_ex": (
+        _I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), _I, ctypes.POINTER(_P)]),
     "sphericart_batch_execute": (_I, [_P, _P]),
     "sphericart_batch_plan_destroy": (_I, [_P]),
     "sphericart_batch_plan_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),

@@ -277,16 +277,18 @@ def device_status() -> int:
 
 
 class BatchPlan:
-    """A ragged batch evaluated by one persistent launch (FP32, l_max <= 16).
+    """A ragged batch evaluated by persistent launches (FP32, l_max <= 16).
 
     ``xyz_list``: CUDA float32 tensors [n_s, 3]; ``lmax_list``: l_max per set.
     Outputs are allocated here (``self.sph[s]`` [n_s, K_s], ``self.dsph[s]``
     [n_s, 3, K_s] when ``gradients``) unless ``outputs`` supplies them.
-    ``execute()`` enqueues the launch on torch's current stream; it can be
-    captured in a CUDA graph.
+    ``mode``: "per_lmax" (one launch per distinct l_max, the default) or
+    "one_launch" (a single launch for every set). ``execute()`` enqueues the
+    launches on torch's current stream; it can be captured in a CUDA graph.
     """
 
-    def __init__(self, xyz_list, lmax_list, normalized=False, gradients=True, launch=None, outputs=None):
+    def __init__(self, xyz_list, lmax_list, normalized=False, gradients=True, launch=None, outputs=None,
+                 mode="per_lmax"):
         import ctypes
 
         if len(xyz_list) != len(lmax_list) or not xyz_list:
@@ -314,8 +316,11 @@ class BatchPlan:
             )
         self._plan = ctypes.c_void_p()
         C.check(
-            "sphericart_batch_plan_create",
-            C.lib().sphericart_batch_plan_create(arr, len(xyz_list), _launch(launch), ctypes.byref(self._plan)),
+            "sphericart_batch_plan_create_ex",
+            C.lib().sphericart_batch_plan_create_ex(
+                arr, len(xyz_list), _launch(launch), {"per_lmax": C.SPH_BATCH_PER_LMAX,
+                                                      "one_launch": C.SPH_BATCH_ONE_LAUNCH}[mode],
+                ctypes.byref(self._plan)),
         )
 
     def execute(self):

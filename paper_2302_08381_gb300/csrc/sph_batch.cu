@@ -1,19 +1,26 @@
-// Ragged batches in ONE persistent launch.
+// Ragged batches in persistent launches.
 //
 // Many point sets (e.g. the neighbour lists of many structures), each with its
-// own l_max <= SPH_MAX_L_POINT, are evaluated by a single kernel: every warp
-// pulls work tiles from a device counter, finds the tile's set by binary
-// search over the per-set tile prefix sums, and runs the POINT recursion for
-// that set's l_max (a switch over compile-time l_max). Tiles are sized per set
-// so that one tile's outputs fill a fixed shared-memory budget per warp: small
-// l_max sets get up to 256-point tiles (each lane computes several points),
-// large ones fewer than 32 points (idle lanes cost arithmetic, which is cheap
-// here, not bandwidth). Sets are ordered by decreasing l_max so the expensive
-// tiles start first and warps mostly run the same l_max body together.
+// own l_max <= SPH_MAX_L_POINT, are evaluated by persistent kernels: every
+// warp pulls work tiles from a device counter, finds the tile's set by a
+// forward scan over the per-set tile prefix sums, and runs the POINT recursion
+// for that set's l_max. Tiles are sized per set so that one tile's outputs fill
+// a shared-memory budget per warp: small l_max sets get up to 256-point tiles
+// (each lane computes several points), large ones fewer than 32 points (idle
+// lanes cost arithmetic, which is cheap here, not bandwidth). Sets are ordered
+// by decreasing l_max.
 //
-// The work list lives in device memory owned by the plan; executing the plan
-// is a counter reset plus one launch on the caller's stream, which can be
-// captured in a CUDA graph.
+// Two plan modes:
+//  * one launch per l_max class (SPH_BATCH_PER_LMAX, the default): the sets of
+//    one l_max form a contiguous tile range run by a kernel compiled for that
+//    l_max only, with its own tile counter and a shared-memory size fitted to
+//    that class's tile -- no branch over l_max in the hot loop, one body in the
+//    instruction cache, occupancy set per class;
+//  * one launch for the whole batch (SPH_BATCH_ONE_LAUNCH): a switch over the
+//    compile-time l_max bodies, shared memory sized for the largest tile.
+// The work list and counters live in device memory owned by the plan;
+// executing the plan is one counter reset plus the launches on the caller's
+// stream, which can be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,179 +28,31 @@
 #include <numeric>
 #include <vector>
 
-#include "sph_point.cuh"
+#include "sph_batch.cuh"
 
 namespace sph {
 
-constexpr int kBatchMaxTile = 256;  // points per batch tile (8 per lane)
-
-struct BatchSet {
-    const float* xyz;
-    float* sph;
-    float* dsph;
-    int64_t n;
-    int64_t tile_begin;  // prefix sum of tiles over the (sorted) sets
-    int32_t L;
-    int32_t P;           // points per tile for this set
-    int32_t norm;
-    int32_t bulk;        // outputs 16-byte aligned: bulk copies allowed
-};
-
-template <int K>
-struct BatchVis {
-    float* rv;
-    float* rd;  // nullptr: values only
-    float ux, uy, uz, ir;
-    int norm;
-    __device__ __forceinline__ void emit(int l, int k, Deriv<float> d) {
-        rv[k] = d.v;
-        if (rd) {
-            if (norm) normalize_deriv<false>(d, l, ux, uy, uz, ir);
-            rd[k] = d.gx;
-            rd[K + k] = d.gy;
-            rd[2 * K + k] = d.gz;
-        }
-    }
-};
-
-template <int L>
-__device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigned char* buf,
-                                           const PointTabs<16, float, false>& tb, int lane, float px, float py,
-                                           float pz) {
-    constexpr int K = (L + 1) * (L + 1);
-    using RS = RowStride<L>;
-    const int P = s.P;
-    const int64_t p0 = t * P;
-    const int cnt = int(min(int64_t(P), s.n - p0));
-    float* s_v = reinterpret_cast<float*>(buf);
-    float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * RS::V * 4));
-    const bool grad = s.dsph != nullptr;
-    // A tile may hold more than 32 points (small l_max): lane j computes the
-    // rows j, j+32, ... so that every set's tile fills the per-warp budget.
-    for (int row = lane; row < cnt; row += 32) {
-        const int64_t p = p0 + row;
-        // the first row's coordinates were prefetched by the caller
-        float x = px, y = py, z = pz;
-        if (row != lane) {
-            x = s.xyz[3 * p];
-            y = s.xyz[3 * p + 1];
-            z = s.xyz[3 * p + 2];
-        }
-        float r2, ir = 1.f;
-        if (s.norm) {
-            unit_point(x, y, z, r2, ir);
-        } else {
-            r2 = x * x + y * y + z * z;
-        }
-        BatchVis<K> vis{s_v + size_t(row) * RS::V, grad ? s_d + size_t(row) * RS::D : nullptr, x, y, z, ir, s.norm};
-        // The l_max = 16 table holds every l <= 16 with the same layout
-        // prefix (entry (l, m) at l(l+1)/2 + m), so it serves every L.
-        point_core<L, true, false>(x, y, z, r2, tb, vis);
-    }
-    if constexpr (RS::PAD) {  // even K: odd-stride rows, coalesced plain copy-out
-        __syncwarp();
-        warp_rows_out<K>(s.sph + p0 * K, s_v, cnt, RS::V, lane);
-        if (grad) warp_rows_out<3 * K>(s.dsph + p0 * 3 * K, s_d, cnt, RS::D, lane);
-        __syncwarp();
-        return;
-    }
-    fence_proxy_async_smem();
-    __syncwarp();
-    const int64_t ev = int64_t(cnt) * K;
-    int64_t ev_bulk = 0, ed_bulk = 0;
-    if (s.bulk) {
-        ev_bulk = (ev * 4) / 16 * 4;
-        ed_bulk = grad ? (3 * ev * 4) / 16 * 4 : 0;
-        if (lane == 0) {
-            if (ev_bulk) bulk_store(s.sph + p0 * K, s_v, uint32_t(ev_bulk * 4));
-            if (ed_bulk) bulk_store(s.dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * 4));
-            bulk_commit();
-        }
-    }
-    for (int64_t i = ev_bulk + lane; i < ev; i += 32) s.sph[p0 * K + i] = s_v[i];
-    if (grad)
-        for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) s.dsph[p0 * 3 * K + i] = s_d[i];
-    if (s.bulk && lane == 0) bulk_wait_read_all();
-    __syncwarp();
+const BatchTabs& batch_tabs() {
+    static const BatchTabs t{make_point_tabs<16, float, false>()};
+    return t;
 }
 
-// Tables of Eq. iter-q / iter-deri for l <= 16, shared by every set.
-struct BatchTabs {
-    PointTabs<16, float, false> t;
+// One launch of a plan: the sets [set_begin, set_end) and their tiles.
+struct BatchLaunch {
+    int L = -1;   // l_max of every set in the range, or -1 (all l_max, one launch)
+    int gn = -1;  // gradients + 2 * normalized of every set in the range, or -1
+    int set_begin = 0, set_end = 0;
+    int64_t tile_begin = 0, tile_end = 0;
+    int per_warp_bytes = 0;
+    int W = 1;  // warps per block
+    int blocks = 1;
+    size_t smem = 0;
 };
 
-constexpr int kBatchRun = 4;  // consecutive tiles a warp takes per counter increment
-
-__global__ void __launch_bounds__(256) batch_kernel(const BatchSet* __restrict__ sets, int nsets,
-                                                    int64_t total_tiles, unsigned long long* __restrict__ counter,
-                                                    int per_warp_bytes, const __grid_constant__ BatchTabs tabs) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char* buf = smem + size_t(warp) * per_warp_bytes;
-    // Warps take runs of kBatchRun consecutive tiles from the counter (the
-    // next run is requested one run ahead). Runs are handed out in increasing
-    // order, so each warp finds a tile's set by scanning forward from the set
-    // of its previous tile, and prefetches the next tile's coordinates while
-    // the current tile is computed.
-    unsigned long long run = 0, nrun = 0;
-    if (lane == 0) run = atomicAdd(counter, 1ull);
-    run = __shfl_sync(0xffffffffu, run, 0);
-    if (lane == 0) nrun = atomicAdd(counter, 1ull);
-    int si = 0;
-    BatchSet s = sets[0];
-    int64_t s_end = (nsets > 1) ? sets[1].tile_begin : total_tiles;
-    auto locate = [&](int64_t t) {  // forward scan: t never decreases for a warp
-        while (t >= s_end && si + 1 < nsets) {
-            ++si;
-            s = sets[si];
-            s_end = (si + 1 < nsets) ? sets[si + 1].tile_begin : total_tiles;
-        }
-    };
-    auto prefetch = [&](int64_t t, float& x, float& y, float& z) {
-        const int64_t p = (t - s.tile_begin) * s.P + lane;
-        if (lane < s.P && p < s.n) {
-            x = s.xyz[3 * p];
-            y = s.xyz[3 * p + 1];
-            z = s.xyz[3 * p + 2];
-        }
-    };
-    int64_t t = int64_t(run) * kBatchRun;
-    float px = 0.f, py = 0.f, pz = 0.f;
-    if (t < total_tiles) {
-        locate(t);
-        prefetch(t, px, py, pz);
-    }
-    while (t < total_tiles) {
-        // next tile: the following one in this run, else the first of the next run
-        int64_t tn = t + 1;
-        if (tn % kBatchRun == 0) {
-            const unsigned long long r = __shfl_sync(0xffffffffu, nrun, 0);
-            tn = int64_t(r) * kBatchRun;
-            if (lane == 0) nrun = atomicAdd(counter, 1ull);
-        }
-        const BatchSet cur = s;
-        const int64_t lt = t - cur.tile_begin;
-        const float cx = px, cy = py, cz = pz;
-        if (tn < total_tiles) {
-            locate(tn);
-            prefetch(tn, px, py, pz);
-        }
-        switch (cur.L) {
-#define SPH_CASE(LL) \
-    case LL:         \
-        batch_tile<LL>(cur, lt, buf, tabs.t, lane, cx, cy, cz); \
-        break;
-            SPH_CASE(0) SPH_CASE(1) SPH_CASE(2) SPH_CASE(3) SPH_CASE(4) SPH_CASE(5) SPH_CASE(6) SPH_CASE(7)
-            SPH_CASE(8) SPH_CASE(9) SPH_CASE(10) SPH_CASE(11) SPH_CASE(12) SPH_CASE(13) SPH_CASE(14)
-            SPH_CASE(15) SPH_CASE(16)
-#undef SPH_CASE
-            default:
-                break;
-        }
-        t = tn;
-    }
-    if (lane == 0) bulk_wait_all();
+int batch_run(const BatchLaunch& b, const BatchSet* sets, unsigned long long* counter, void* stream, int* occ_out) {
+    BatchClassArgs a{sets, b.set_begin, b.set_end, b.tile_begin, b.tile_end, counter, b.per_warp_bytes, b.W,
+                     b.blocks, b.smem, stream, occ_out, b.gn};
+    return b.L >= 0 ? batch_class_fn(b.L)(a) : batch_kernel_run<-1, -1>(a);
 }
 
 }  // namespace sph
@@ -203,22 +62,15 @@ using namespace sph;
 struct sph_batch_plan {
     int device = -1;
     int nsets = 0;
+    int mode = SPH_BATCH_PER_LMAX;
     int64_t total_points = 0;
     int64_t total_tiles = 0;
     BatchSet* d_sets = nullptr;
-    unsigned long long* d_counter = nullptr;
-    int warps_per_block = 1;
-    int blocks = 1;
-    int per_warp_bytes = 0;
-    size_t smem = 0;
+    unsigned long long* d_counter = nullptr;  // one counter per launch
+    std::vector<BatchLaunch> launches;
 };
 
 namespace {
-
-const BatchTabs& batch_tabs() {
-    static const BatchTabs t{make_point_tabs<16, float, false>()};
-    return t;
-}
 
 int tile_mult4(int L) {
     const int K = (L + 1) * (L + 1);
@@ -230,8 +82,12 @@ int tile_mult4(int L) {
 
 extern "C" {
 
-int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph_launch* launch,
-                                 sph_batch_plan** plan_out) {
+int sphericart_batch_plan_create_ex(const sph_batch_set* sets, int nsets, const sph_launch* launch, int mode,
+                                    sph_batch_plan** plan_out) {
+    if (mode != SPH_BATCH_PER_LMAX && mode != SPH_BATCH_ONE_LAUNCH) {
+        set_error("batch_plan_create: mode=%d is not an sph_batch_mode", mode);
+        return SPH_EINVAL;
+    }
     if (!plan_out || !sets || nsets <= 0) {
         set_error("batch_plan_create: sets, nsets > 0 and plan are required");
         return SPH_EINVAL;
@@ -269,13 +125,24 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
     // Per-warp shared-memory budget: one 32-point l_max = 8 value+gradient tile.
     const int budget = lau.points_per_tile > 0 ? lau.points_per_tile * 1296 : 32 * 1296;
 
+    // PER_LMAX without an explicit launch shape: every l_max class takes the
+    // tile size and warps per block of the single-set POINT kernel for that
+    // l_max (tuned if installed, else its default); otherwise one per-warp
+    // budget for all sets.
+    const bool class_shapes = mode == SPH_BATCH_PER_LMAX && lau.points_per_tile == 0 && lau.warps_per_block == 0;
     std::vector<int> order(nsets);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].l_max > sets[b].l_max; });
+    // sets ordered by decreasing l_max, then by (gradients, normalized): every
+    // class of equal (l_max, gradients, normalized) is a contiguous range
+    auto gn_of = [&](int i) { return (sets[i].dsph ? 1 : 0) + (sets[i].normalized ? 2 : 0); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (sets[a].l_max != sets[b].l_max) return sets[a].l_max > sets[b].l_max;
+        return gn_of(a) < gn_of(b);
+    });
     std::vector<BatchSet> hs;
     hs.reserve(nsets);
+    std::vector<int> bytes_of(nsets);
     int64_t tiles = 0, points = 0;
-    int max_bytes = 0;
     for (int oi : order) {
         const sph_batch_set& s = sets[oi];
         const int L = s.l_max;
@@ -286,8 +153,8 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         const int mult = tile_mult4(L);
         int P = std::min(kBatchMaxTile, std::max(1, budget / row));
         P = std::max(mult, P / mult * mult);
-        const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
-        max_bytes = std::max(max_bytes, bytes);
+        if (class_shapes) P = point_fwd_shape(L, grad).points_per_tile;  // a multiple of mult, <= 32
+        bytes_of[hs.size()] = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
         BatchSet b{};
         b.xyz = s.xyz;
         b.sph = s.sph;
@@ -302,21 +169,41 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         points += s.n;
         hs.push_back(b);
     }
-    const size_t smem = size_t(W) * size_t(max_bytes);
-    if (smem > size_t(max_smem_optin())) {
-        set_error("batch plan needs %zu bytes of shared memory per block", smem);
-        return SPH_EINVAL;
+    // The launches: one per run of equal (l_max, gradients, normalized) (sets
+    // are sorted), or one for all.
+    auto gn_hs = [&](int i) { return (hs[i].dsph ? 1 : 0) + (hs[i].norm ? 2 : 0); };
+    std::vector<BatchLaunch> launches;
+    for (int i = 0; i < nsets;) {
+        int j = i;
+        int bytes = 0;
+        while (j < nsets && (mode == SPH_BATCH_ONE_LAUNCH || (hs[j].L == hs[i].L && gn_hs(j) == gn_hs(i))))
+            bytes = std::max(bytes, bytes_of[j++]);
+        BatchLaunch bl;
+        bl.L = mode == SPH_BATCH_ONE_LAUNCH ? -1 : hs[i].L;
+        bl.gn = mode == SPH_BATCH_ONE_LAUNCH ? -1 : gn_hs(i);
+        bl.set_begin = i;
+        bl.set_end = j;
+        bl.tile_begin = hs[i].tile_begin;
+        bl.tile_end = (j < nsets) ? hs[j].tile_begin : tiles;
+        bl.per_warp_bytes = bytes;
+        bl.W = class_shapes ? point_fwd_shape(hs[i].L, hs[i].dsph ? 1 : 0).warps_per_block : W;
+        bl.smem = size_t(bl.W) * size_t(bytes);
+        if (bl.smem > size_t(max_smem_optin())) {
+            set_error("batch plan needs %zu bytes of shared memory per block", bl.smem);
+            return SPH_EINVAL;
+        }
+        if (bl.tile_end > bl.tile_begin) launches.push_back(bl);
+        i = j;
     }
     auto* plan = new sph_batch_plan();
     plan->device = dev;
     plan->nsets = nsets;
+    plan->mode = mode;
     plan->total_points = points;
     plan->total_tiles = tiles;
-    plan->warps_per_block = W;
-    plan->per_warp_bytes = max_bytes;
-    plan->smem = smem;
+    const size_t ncount = std::max<size_t>(1, launches.size());
     if (cudaMalloc(&plan->d_sets, sizeof(BatchSet) * hs.size()) != cudaSuccess ||
-        cudaMalloc(&plan->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&plan->d_counter, sizeof(unsigned long long) * ncount) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(plan->d_sets);
         delete plan;
@@ -324,7 +211,14 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         return SPH_ENOMEM;
     }
     cudaError_t e = cudaMemcpy(plan->d_sets, hs.data(), sizeof(BatchSet) * hs.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = ensure_smem(batch_kernel, smem);
+    for (BatchLaunch& bl : launches) {  // shared-memory attribute and persistent grid of every launch
+        if (e != cudaSuccess) break;
+        int occ = 1;
+        e = static_cast<cudaError_t>(batch_run(bl, plan->d_sets, plan->d_counter, nullptr, &occ));
+        const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, occ) : occ;
+        const int64_t want = (bl.tile_end - bl.tile_begin + bl.W - 1) / bl.W;
+        bl.blocks = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    }
     if (e != cudaSuccess) {
         cudaFree(plan->d_sets);
         cudaFree(plan->d_counter);
@@ -332,15 +226,14 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph
         set_error("batch plan: %s", cudaGetErrorString(e));
         return SPH_ECUDA;
     }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(batch_kernel), 32 * W,
-                                                      smem) != cudaSuccess)
-        occ = 1;
-    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    const int64_t want = (tiles + W - 1) / W;
-    plan->blocks = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    plan->launches = std::move(launches);
     *plan_out = plan;
     return SPH_OK;
+}
+
+int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets, const sph_launch* launch,
+                                 sph_batch_plan** plan_out) {
+    return sphericart_batch_plan_create_ex(sets, nsets, launch, SPH_BATCH_PER_LMAX, plan_out);
 }
 
 int sphericart_batch_execute(const sph_batch_plan* plan, void* stream) {
@@ -348,18 +241,15 @@ int sphericart_batch_execute(const sph_batch_plan* plan, void* stream) {
         set_error("batch_execute: plan is NULL");
         return SPH_EINVAL;
     }
-    if (plan->total_tiles == 0) return SPH_OK;
+    if (plan->launches.empty()) return SPH_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long), st);
+    cudaError_t e =
+        cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long) * plan->launches.size(), st);
+    for (size_t i = 0; i < plan->launches.size() && e == cudaSuccess; ++i)
+        e = static_cast<cudaError_t>(
+            batch_run(plan->launches[i], plan->d_sets, plan->d_counter + i, stream, nullptr));
     if (e != cudaSuccess) {
         set_error("batch_execute: %s", cudaGetErrorString(e));
-        return SPH_ECUDA;
-    }
-    batch_kernel<<<plan->blocks, 32 * plan->warps_per_block, plan->smem, st>>>(
-        plan->d_sets, plan->nsets, plan->total_tiles, plan->d_counter, plan->per_warp_bytes, batch_tabs());
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error("batch_execute launch: %s", cudaGetErrorString(e));
         return SPH_ECUDA;
     }
     return SPH_OK;
@@ -524,22 +414,24 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
     // returns, so the staging may be reused by the next call.
     cudaError_t e = cudaMemcpyAsync(d_sets, g_noalloc_host, sizeof(BatchSet) * size_t(nsets), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = ensure_smem(batch_kernel, smem);
+    BatchLaunch bl;  // one launch for every l_max, as SPH_BATCH_ONE_LAUNCH
+    bl.W = W;
+    bl.set_begin = 0;
+    bl.set_end = nsets;
+    bl.tile_begin = 0;
+    bl.tile_end = tiles;
+    bl.per_warp_bytes = max_bytes;
+    bl.smem = smem;
+    int occ = 1;
+    if (e == cudaSuccess) e = static_cast<cudaError_t>(batch_run(bl, d_sets, d_counter, stream, &occ));
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("batch_compute_noalloc: %s", cudaGetErrorString(e));
         return SPH_ECUDA;
     }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(batch_kernel), 32 * W,
-                                                      smem) != cudaSuccess) {
-        cudaGetLastError();
-        occ = 1;
-    }
-    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((tiles + W - 1) / W, int64_t(bps) * sm_count())));
-    batch_kernel<<<blocks, 32 * W, smem, st>>>(d_sets, nsets, tiles, d_counter, max_bytes, batch_tabs());
-    e = cudaGetLastError();
+    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, occ) : occ;
+    bl.blocks = int(std::max<int64_t>(1, std::min<int64_t>((tiles + W - 1) / W, int64_t(bps) * sm_count())));
+    e = static_cast<cudaError_t>(batch_run(bl, d_sets, d_counter, stream, nullptr));
     if (e != cudaSuccess) {
         set_error("batch_compute_noalloc launch: %s", cudaGetErrorString(e));
         return SPH_ECUDA;

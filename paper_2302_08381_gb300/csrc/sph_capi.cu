@@ -256,6 +256,15 @@ bool resolve_point(sph_launch& s, const sph_launch& dflt, int L, int elem, size_
 
 }  // namespace
 
+sph_launch point_fwd_shape(int L, int grad) {
+    sph_launch s{0, 0, 0, 0};
+    if (!tuned_launch(L, SPH_F32, SPH_OUT_SAME, grad, &s)) s = sph_launch{0, 0, 0, 0};
+    const sph_launch d = default_point_fwd(L, grad, 4, 0);
+    if (s.points_per_tile == 0) s.points_per_tile = d.points_per_tile;
+    if (s.warps_per_block == 0) s.warps_per_block = d.warps_per_block;
+    return s;
+}
+
 bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s) {
     int d = -1;
     if (cudaGetDevice(&d) != cudaSuccess) {

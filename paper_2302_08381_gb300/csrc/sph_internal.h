@@ -111,9 +111,19 @@ PointFwdFn point_fwd_fn(int L);
 PointBwdFn point_bwd_fn(int L);
 PointBwdFn point_dbwd_fn(int L);
 
+// Ragged-batch kernel of one compile-time l_max (one object file per l_max).
+struct BatchClassArgs;
+using BatchClassFn = int (*)(const BatchClassArgs&);
+BatchClassFn batch_class_fn(int L);
+
 // Tuned POINT forward shape installed for (l_max, dtype, out, grad) on the
 // current device; false if none.
 bool tuned_launch(int L, int dtype, int out, int grad, sph_launch* s);
+
+// The POINT forward launch shape for FP32 values (+ gradients when grad) at
+// this l_max on the current device: the tuned one if installed, else the
+// default (points_per_tile and warps_per_block resolved).
+sph_launch point_fwd_shape(int L, int grad);
 
 // Bytes of one output row of the POINT forward for this request.
 size_t point_row_bytes(int L, int grad, int elem, int hess = 0);

@@ -1,7 +1,7 @@
 // Instantiates the POINT kernels for one compile-time l_max. The build
 // compiles this file once per l_max in [0, SPH_MAX_L_POINT] with
 // -DSPH_INST_L=<l_max>, in parallel.
-#include "sph_point.cuh"
+#include "sph_batch.cuh"
 
 #ifndef SPH_INST_L
 #error "compile with -DSPH_INST_L=<l_max>"
@@ -50,6 +50,23 @@ int SPH_CAT(point_dbwd_L, SPH_INST_L)(const BwdArgs& a) {
     if (a.dtype == SPH_F64)
         return a.normalized ? launch_point_bwd<L, true, true, double>(a) : launch_point_bwd<L, false, true, double>(a);
     return a.normalized ? launch_point_bwd<L, true, true, float>(a) : launch_point_bwd<L, false, true, float>(a);
+}
+
+// The ragged-batch kernel restricted to this l_max (one launch per l_max
+// class of a batch plan).
+int SPH_CAT(batch_class_L, SPH_INST_L)(const BatchClassArgs& a) {
+    switch (a.gn) {
+        case 0:
+            return batch_kernel_run<SPH_INST_L, 0>(a);
+        case 1:
+            return batch_kernel_run<SPH_INST_L, 1>(a);
+        case 2:
+            return batch_kernel_run<SPH_INST_L, 2>(a);
+        case 3:
+            return batch_kernel_run<SPH_INST_L, 3>(a);
+        default:
+            return batch_kernel_run<SPH_INST_L, -1>(a);
+    }
 }
 
 }  // namespace sph

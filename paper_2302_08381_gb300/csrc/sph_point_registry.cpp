@@ -1,4 +1,4 @@
-// Table of the per-l_max POINT launchers (one object file per l_max).
+// Table of the per-l_max POINT and batch-class launchers (one object file per l_max).
 #include "sph_internal.h"
 
 namespace sph {
@@ -6,7 +6,8 @@ namespace sph {
 #define SPH_DECL(L)                          \
     int point_fwd_L##L(const FwdArgs&);      \
     int point_bwd_L##L(const BwdArgs&);      \
-    int point_dbwd_L##L(const BwdArgs&);
+    int point_dbwd_L##L(const BwdArgs&);     \
+    int batch_class_L##L(const BatchClassArgs&);
 SPH_DECL(0) SPH_DECL(1) SPH_DECL(2) SPH_DECL(3) SPH_DECL(4) SPH_DECL(5) SPH_DECL(6) SPH_DECL(7) SPH_DECL(8)
 SPH_DECL(9) SPH_DECL(10) SPH_DECL(11) SPH_DECL(12) SPH_DECL(13) SPH_DECL(14) SPH_DECL(15) SPH_DECL(16)
 #undef SPH_DECL
@@ -29,6 +30,13 @@ static const PointBwdFn kDbwd[] = {SPH_ROW(0),  SPH_ROW(1),  SPH_ROW(2),  SPH_RO
                                    SPH_ROW(12), SPH_ROW(13), SPH_ROW(14), SPH_ROW(15), SPH_ROW(16)};
 #undef SPH_ROW
 
+#define SPH_ROW(L) batch_class_L##L
+static const BatchClassFn kBatch[] = {SPH_ROW(0),  SPH_ROW(1),  SPH_ROW(2),  SPH_ROW(3),  SPH_ROW(4),  SPH_ROW(5),
+                                      SPH_ROW(6),  SPH_ROW(7),  SPH_ROW(8),  SPH_ROW(9),  SPH_ROW(10), SPH_ROW(11),
+                                      SPH_ROW(12), SPH_ROW(13), SPH_ROW(14), SPH_ROW(15), SPH_ROW(16)};
+#undef SPH_ROW
+
+BatchClassFn batch_class_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kBatch[L] : nullptr; }
 PointFwdFn point_fwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kFwd[L] : nullptr; }
 PointBwdFn point_bwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kBwd[L] : nullptr; }
 PointBwdFn point_dbwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kDbwd[L] : nullptr; }

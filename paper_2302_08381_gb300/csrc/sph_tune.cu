@@ -133,14 +133,18 @@ int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream
     EventPair ev;
     float best_t = 1e30f;
     sph_launch best_s{0, 0, 0, 0};
-    // points_per_tile here scales the per-warp budget (in l_max = 8 gradient rows).
-    const int budgets[] = {64, 48, 32, 24, 16, 12, 8};
+    // points_per_tile here scales the per-warp budget (in l_max = 8 gradient
+    // rows); budget 0 with 0 warps per block is the plan's per-l_max shape
+    // (every l_max class on its single-set POINT shape).
+    const int budgets[] = {0, 64, 48, 32, 24, 16, 12, 8};
     const int Ws[] = {1, 2, 4};
     const int Bs[] = {0, 2, 3, 4, 8, 16};
+    bool found = false;
     for (int bud : budgets)
         for (int W : Ws)
             for (int B : Bs) {
-                sph_launch s{bud, W, B, 0};
+                if (bud == 0 && W != 1) continue;
+                sph_launch s{bud, bud == 0 ? 0 : W, B, 0};
                 sph_batch_plan* plan = nullptr;
                 if (sphericart_batch_plan_create(sets, nsets, &s, &plan) != SPH_OK) {
                     cudaGetLastError();
@@ -164,9 +168,10 @@ int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream
                 if (t < best_t) {
                     best_t = t;
                     best_s = s;
+                    found = true;
                 }
             }
-    if (best_s.points_per_tile == 0) {
+    if (!found) {
         set_error("batch_autotune: no launchable shape");
         return SPH_EUNSUPPORTED;
     }

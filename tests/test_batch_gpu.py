@@ -20,10 +20,11 @@ def _sets(nsets, choices, nmin, nmax, seed):
     return [xt[offs[i]:offs[i + 1]] for i in range(nsets)], [int(v) for v in lmax], xyz, offs
 
 
+@pytest.mark.parametrize("mode", ["per_lmax", "one_launch"])
 @pytest.mark.parametrize("normalized", [False, True])
-def test_batch_matches_single_launch_and_oracle(normalized):
+def test_batch_matches_single_launch_and_oracle(normalized, mode):
     xs, ls, xyz, offs = _sets(40, list(range(0, 17)), 1, 3000, seed=300)
-    plan = api.BatchPlan(xs, ls, normalized=normalized)
+    plan = api.BatchPlan(xs, ls, normalized=normalized, mode=mode)
     plan.execute()
     torch.cuda.synchronize()
     for i, (x, L) in enumerate(zip(xs, ls)):
@@ -45,10 +46,11 @@ def test_batch_matches_single_launch_and_oracle(normalized):
     plan.close()
 
 
-def test_batch_values_only_and_empty_sets():
+@pytest.mark.parametrize("mode", ["per_lmax", "one_launch"])
+def test_batch_values_only_and_empty_sets(mode):
     xs, ls, xyz, offs = _sets(12, [3, 6, 8, 12], 1, 500, seed=301)
     xs[3] = xs[3][:0]
-    plan = api.BatchPlan(xs, ls, gradients=False)
+    plan = api.BatchPlan(xs, ls, gradients=False, mode=mode)
     plan.execute()
     torch.cuda.synchronize()
     for i, (x, L) in enumerate(zip(xs, ls)):
@@ -58,9 +60,10 @@ def test_batch_values_only_and_empty_sets():
             assert_values(plan.sph[i].double().cpu().numpy(), x.double().cpu().numpy(), L, False, F32_VAL, ref=ref)
 
 
-def test_batch_graph_capture_replay():
+@pytest.mark.parametrize("mode", ["per_lmax", "one_launch"])
+def test_batch_graph_capture_replay(mode):
     xs, ls, _, _ = _sets(64, [3, 6, 8, 12], 1000, 20000, seed=302)
-    plan = api.BatchPlan(xs, ls)
+    plan = api.BatchPlan(xs, ls, mode=mode)
     plan.execute()
     torch.cuda.synchronize()
     want = [s.clone() for s in plan.sph]
@@ -78,3 +81,24 @@ def test_batch_graph_capture_replay():
     torch.cuda.synchronize()
     for a, b in zip(plan.sph, want):
         assert torch.equal(a, b)
+
+
+def test_batch_modes_agree():
+    """One launch per l_max class and one launch for all sets compute the same
+    outputs (the same recursion in separately compiled kernels: equal up to a
+    few FP32 roundings on the l-block scales)."""
+    xs, ls, xyz, offs = _sets(80, [0, 2, 3, 6, 8, 12, 16], 1, 6000, seed=303)
+    a = api.BatchPlan(xs, ls, mode="per_lmax")
+    b = api.BatchPlan(xs, ls, mode="one_launch")
+    a.execute()
+    b.execute()
+    torch.cuda.synchronize()
+    for i, L in enumerate(ls):
+        p = xyz[offs[i]:offs[i + 1]].astype(np.float64)
+        if not p.shape[0]:
+            continue
+        dv = (a.sph[i] - b.sph[i]).abs().double().cpu().numpy() / value_scale(p, L, False)
+        dg = (a.dsph[i] - b.dsph[i]).abs().double().cpu().numpy() / grad_scale(p, L, False)[:, None, :]
+        assert dv.max() < 5e-6 and dg.max() < 5e-6, (i, L, dv.max(), dg.max())
+    a.close()
+    b.close()

@@ -211,6 +211,14 @@ def test_argument_errors_before_any_cuda_call():
     assert _err(C.sphericart_backward, 16, 16, 4, 6, 0, 0, 0, launch, none, none) == C.SPH_EINVAL
     assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, 1, launch, 16, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_double_backward, 16, 16, none, 4, 6, 0, 0, 0, launch, 16, 16, none) == C.SPH_EINVAL
+    # batch plan mode
+    import ctypes
+
+    arr = (C.sph_batch_set * 1)()
+    arr[0] = C.sph_batch_set(16, 16, None, 4, 3, 0)
+    h = ctypes.c_void_p()
+    assert C.lib().sphericart_batch_plan_create_ex(arr, 1, None, 7, ctypes.byref(h)) == C.SPH_EINVAL
+    assert "mode" in C.last_error()
     # host table
     with pytest.raises(C.SphericartError):
         C.sphericart_host_table(200, 0)

@@ -62,8 +62,10 @@ def _assert_close(outs, plan, xyz, offs, ls, normalized):
 def test_noalloc_batch_matches_plan_on_two_calls_in_a_row():
     xs1, ls1, xyz1, offs1 = _batch(48, [3, 6, 8, 12], 100, 20000, seed=500)
     xs2, ls2, xyz2, offs2 = _batch(17, list(range(0, 17)), 1, 5000, seed=501)
-    plan1 = api.BatchPlan(xs1, ls1)
-    plan2 = api.BatchPlan(xs2, ls2, normalized=True)
+    # the no-allocation entry point runs the single-launch kernel: compare with
+    # plans of the same mode
+    plan1 = api.BatchPlan(xs1, ls1, mode="one_launch")
+    plan2 = api.BatchPlan(xs2, ls2, normalized=True, mode="one_launch")
     plan1.execute()
     plan2.execute()
     out1 = _noalloc(xs1, ls1)
