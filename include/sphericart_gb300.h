@@ -101,7 +101,8 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
  *           registers, degree l uniform across the lanes); each point's output
  *           rows are staged in shared memory in windows of whole degrees and
  *           written with TMA bulk copies of 32-byte-aligned runs (~1 KB and
- *           longer, which GB300's HBM needs for full write bandwidth). */
+ *           longer, which GB300's HBM needs for full write bandwidth). Also a
+ *           fused backward (sphericart_backward). */
 typedef enum {
     SPH_KERNEL_AUTO = 0,
     SPH_KERNEL_POINT = 1,
@@ -181,8 +182,10 @@ int sphericart_compute_host(const void* xyz_host, int64_t n, int l_max, int norm
  * contracts the dsph materialised by the forward pass (Section 3); that path
  * is sphericart_compute + a contraction.
  *   xyz [n,3], g [n,K], dxyz [n,3], all of `dtype` (device).
- * Errors as sphericart_compute_ex (kernel: AUTO, POINT or SLICE; the DEGREE
- * families return SPH_EUNSUPPORTED). */
+ * kernel: AUTO (POINT up to SPH_MAX_L_POINT, then ROW for FP32 up to l_max 63,
+ * else SLICE), POINT, SLICE, or ROW (FP32, 16 <= l_max <= 63: 8 lanes per
+ * point, the g rows read by TMA bulk loads of whole-degree windows); the
+ * DEGREE families return SPH_EUNSUPPORTED. Errors as sphericart_compute_ex. */
 int sphericart_backward(const void* xyz, const void* g, int64_t n, int l_max,
                         int normalized, int dtype, int kernel,
                         const sph_launch* launch, void* dxyz, void* stream);

@@ -519,13 +519,28 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
                            void* grad_xyz, void* stream, bool dbw) {
     int st = check_common(n, l_max, dtype, kernel);
     if (st) return st;
-    int fam = kernel == SPH_KERNEL_AUTO ? (l_max <= SPH_MAX_L_POINT ? SPH_KERNEL_POINT : SPH_KERNEL_SLICE) : kernel;
+    // AUTO: POINT within its l_max range; beyond it the fused backward in FP32
+    // runs on ROW (up to its l_max), everything else on SLICE.
+    int fam = kernel;
+    if (fam == SPH_KERNEL_AUTO) {
+        if (l_max <= SPH_MAX_L_POINT)
+            fam = SPH_KERNEL_POINT;
+        else if (!dbw && dtype == SPH_F32 && l_max <= kRowMaxL)
+            fam = SPH_KERNEL_ROW;
+        else
+            fam = SPH_KERNEL_SLICE;
+    }
     if (fam == SPH_KERNEL_POINT && l_max > SPH_MAX_L_POINT) {
         set_error("POINT kernels take l_max <= %d", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
-    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN || fam == SPH_KERNEL_ROW) {
-        set_error("backward passes run on the POINT or SLICE kernels");
+    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN) {
+        set_error("backward passes run on the POINT, ROW (backward) or SLICE kernels");
+        return SPH_EUNSUPPORTED;
+    }
+    if (fam == SPH_KERNEL_ROW && (dbw || dtype != SPH_F32 || l_max < kRowMinL || l_max > kRowMaxL)) {
+        set_error("the ROW backward takes FP32, %d <= l_max <= %d (double backward: POINT or SLICE)", kRowMinL,
+                  kRowMaxL);
         return SPH_EUNSUPPORTED;
     }
     if (n == 0) return SPH_OK;
@@ -557,6 +572,24 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
             return SPH_EINVAL;
         PointBwdFn fn = dbw ? point_dbwd_fn(l_max) : point_bwd_fn(l_max);
         return cuda_status(fn(a), dbw ? "POINT double-backward launch" : "POINT backward launch");
+    }
+    if (fam == SPH_KERNEL_ROW) {
+        if (a.launch.warps_per_block < 0 || a.launch.warps_per_block > 8 || a.launch.blocks_per_sm < 0 ||
+            a.launch.blocks_per_sm > 32) {
+            set_error("ROW launch: warps_per_block must be in [0,8] and blocks_per_sm in [0,32]");
+            return SPH_EINVAL;
+        }
+        a.status = device_status_word();
+        if (!a.status) {
+            set_error("could not allocate the device status word");
+            return SPH_ENOMEM;
+        }
+        const int e2 = (l_max + 1 + 7) / 8 <= 5 ? row_bwd_part0(a) : row_bwd_part1(a);
+        if (e2 == int(cudaErrorInvalidConfiguration)) {
+            set_error("ROW launch shape needs more shared memory per block than the device allows");
+            return SPH_EINVAL;
+        }
+        return cuda_status(e2, "ROW backward launch");
     }
     if (!valid_lanes(a.launch)) return SPH_EINVAL;
     return cuda_status(dbw ? slice_dbwd(a) : slice_bwd(a), dbw ? "SLICE double-backward launch" : "SLICE backward launch");

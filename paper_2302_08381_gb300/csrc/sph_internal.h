@@ -140,6 +140,8 @@ int degree_fwd_down(const FwdArgs& a);
 // part 0 covers 3..5 channels per lane (l_max <= 47), part 1 6..8.
 int row_fwd_part0(const FwdArgs& a);
 int row_fwd_part1(const FwdArgs& a);
+int row_bwd_part0(const BwdArgs& a);  // fused recompute-backward (dxyz), FP32
+int row_bwd_part1(const BwdArgs& a);
 constexpr int kRowMinL = 16;
 constexpr int kRowMaxL = 63;
 

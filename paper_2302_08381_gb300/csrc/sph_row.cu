@@ -300,6 +300,251 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
     if (j == 0) bulk_wait_all();
 }
 
+// ------------------------------------------------------------- backward
+// Fused recompute-backward with the same decomposition: dxyz_i = sum_k g_k
+// dY_k/dx_i (Eq. iter-deri), the recursion recomputed in registers, the
+// upstream-gradient row of each point read in the same windows of whole
+// degrees by TMA bulk loads (double buffered: the next window is in flight
+// while the current one is used), the unaligned window edges by plain loads.
+// Lane j accumulates its channels' terms; the 8 lanes of a point reduce with
+// shuffles at the end. Every mbarrier wait is bounded; a timeout sets the
+// device status word and skips the rest of the launch.
+constexpr int kBPad = 4;                  // slots before a window's first 16-byte-aligned column
+constexpr int kBBuf = kBPad + kCap + 8;   // floats per window buffer
+constexpr uint32_t kRowWaitPolls = 1u << 22;
+
+__host__ __device__ constexpr size_t row_bwd_warp_bytes() {
+    return size_t(kPW) * 2 * kBBuf * sizeof(float) + size_t(kPW) * 2 * sizeof(uint64_t);
+}
+
+// Window of whole degrees starting at degree l: [l, lw).
+__device__ __forceinline__ int row_window_end(int l, int L) {
+    int lw = l + 1;
+    while (lw <= L && (lw + 1) * (lw + 1) - l * l <= kCap - 7) ++lw;
+    return lw;
+}
+
+// Starts loading the columns [c0, c1) of the upstream-gradient row `grow` into
+// `buf` (column c at buf[c - s + kBPad], s = first 16-byte-aligned column >= c0):
+// the aligned middle by one bulk copy completing on `bar` (issued by lane j = 0),
+// the edges by plain loads of the group's lanes. Returns whether a bulk copy was issued.
+__device__ __forceinline__ bool row_window_load(const float* __restrict__ grow, int c0, int c1, float* buf,
+                                                uint64_t* bar, int j) {
+    const int phase = int((reinterpret_cast<uintptr_t>(grow + c0) / sizeof(float)) % 4);
+    const int s = c0 + (4 - phase) % 4;
+    const int e = s + max(0, (c1 - s) / 4 * 4);
+    const bool bulk = e > s;
+    if (bulk && j == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t((e - s) * sizeof(float)));
+        bulk_load(buf + kBPad, grow + s, uint32_t((e - s) * sizeof(float)), bar);
+    }
+    for (int c = c0 + j; c < min(s, c1); c += kG) buf[c - s + kBPad] = grow[c];
+    for (int c = max(e, c0) + j; c < c1; c += kG) buf[c - s + kBPad] = grow[c];
+    return bulk;
+}
+
+template <bool NORM, int NCH>
+__global__ void __launch_bounds__(256) row_bwd_kernel(const float* __restrict__ xyz, const float* __restrict__ g,
+                                                      int64_t n, int L, const float* __restrict__ tb,
+                                                      float inv_sqrt2, float* __restrict__ dxyz,
+                                                      uint32_t* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int gi = lane / kG;  // point of the warp tile
+    const int j = lane % kG;   // channel class m = j (mod 8)
+    unsigned char* wbase = smem + size_t(warp) * row_bwd_warp_bytes();
+    float* const bufs = reinterpret_cast<float*>(wbase) + size_t(gi) * 2 * kBBuf;  // this point's two windows
+    uint64_t* const bars =
+        reinterpret_cast<uint64_t*>(wbase + size_t(kPW) * 2 * kBBuf * sizeof(float)) + 2 * gi;
+    const int64_t K = int64_t(L + 1) * (L + 1);
+    const int64_t ntiles = (n + kPW - 1) / kPW;
+    const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tb);
+    const int nb_lane = (lane & ~(kG - 1)) | ((j + 1) & (kG - 1));
+    const float jf = float(j);
+
+    if (j == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    uint32_t parity = 0;   // bit b: phase of buffer b's next completion (same in the 8 lanes of a point)
+    uint32_t pending = 0;  // bit b: a bulk load into buffer b is in flight
+    bool failed = false;
+
+    for (int64_t tile = int64_t(blockIdx.x) * W + warp; tile < ntiles && !failed; tile += int64_t(gridDim.x) * W) {
+        const int64_t p = tile * kPW + gi;
+        const bool live = p < n;
+        float x = 0.f, y = 0.f, z = 0.f, ir = 1.f;
+        if (live) {
+            x = xyz[3 * p];
+            y = xyz[3 * p + 1];
+            z = xyz[3 * p + 2];
+        }
+        if (NORM) {
+            const float rr = fmaf(x, x, fmaf(y, y, z * z));
+            ir = rr > 0.f ? 1.f / sqrtf(rr) : 0.f;
+            x *= ir;
+            y *= ir;
+            z *= ir;
+        }
+        const float r2 = fmaf(z, z, fmaf(x, x, y * y));
+        const float* grow = g + (live ? p : 0) * K;
+
+        float cm[NCH], sm[NCH], cm1[NCH], sm1[NCH];
+        {
+            const CSf xy{x, y};
+            CSf a{1.f, 0.f}, b{1.f, 0.f}, w8{1.f, 0.f}, p7{1.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < kG; ++t) {
+                if (t < j) a = a.times(xy);
+                if (t < j - 1) b = b.times(xy);
+                if (t < kG - 1) p7 = p7.times(xy);
+                w8 = w8.times(xy);
+            }
+            if (j == 0) b = p7;
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                cm[k] = a.c;
+                sm[k] = a.s;
+                const bool none = (j == 0 && k == 0);
+                cm1[k] = none ? 0.f : b.c;
+                sm1[k] = none ? 0.f : b.s;
+                a = a.times(w8);
+                if (!none) b = b.times(w8);
+            }
+        }
+        float q1[NCH], q2[NCH];
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) q1[k] = q2[k] = 0.f;
+        float4 ta[NCH];
+        float tf[NCH];
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+            ta[k] = t4[0];
+            tf[k] = tb[4];
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f, S = 0.f;
+
+        // window 0 into buffer 0
+        int l = 0, lw = row_window_end(0, L), buf = 0;
+        if (live && row_window_load(grow, 0, lw * lw, bufs, &bars[0], j)) pending |= 1u;
+        while (l <= L) {
+            // next window into the other buffer (free: consumed before the last fence + sync)
+            const int ln = lw, lwn = ln <= L ? row_window_end(ln, L) : ln;
+            if (live && ln <= L && row_window_load(grow, ln * ln, lwn * lwn, bufs + (buf ^ 1) * kBBuf, &bars[buf ^ 1], j))
+                pending |= 1u << (buf ^ 1);
+            // this window's bulk part
+            if (live && (pending & (1u << buf))) {
+                if (mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u, kRowWaitPolls)) {
+                    parity ^= 1u << buf;
+                    pending &= ~(1u << buf);
+                } else {
+                    if (j == 0) atomicOr(status, kStatusLoadTimeout);
+                    failed = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, failed)) {
+                failed = true;
+                break;
+            }
+            __syncwarp();  // edge elements loaded by the other lanes
+            const float* gb = bufs + buf * kBBuf;
+            const int phase = int((reinterpret_cast<uintptr_t>(grow + l * l) / sizeof(float)) % 4);
+            const int s0 = l * l + (4 - phase) % 4;  // column at gb[kBPad]
+            for (int d = l; d < lw; ++d) {
+                const int ctr = d * d + d;
+                const int kend = d / kG;
+                const int dn = d < L ? d + 1 : L;
+                float4 na[NCH];
+                float nf[NCH];
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const int mk = j + kG * k;
+                    const int i = tri(dn, mk <= dn ? mk : dn);
+                    na[k] = t4[2 * i];
+                    nf[k] = tb[8 * i + 4];
+                }
+                const float lf = float(d);
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    if (k > kend) break;
+                    const int m = j + kG * k;
+                    const bool on = m <= d;
+                    const float4 t0 = ta[k];
+                    const float src = (j == 0) ? (k + 1 < NCH ? q1[k + 1 < NCH ? k + 1 : k] : 0.f) : q1[k];
+                    const float qn = __shfl_sync(0xffffffffu, src, nb_lane);
+                    float q = fmaf(t0.x * z, q1[k], fmaf(-(t0.y * r2), q2[k], t0.z));
+                    q = on ? q : 0.f;
+                    if (on) {
+                        const float E1 = t0.w * qn;
+                        const float Qz = tf[k] * q1[k];
+                        const float Qx = x * E1, Qy = y * E1;
+                        const float gp = gb[ctr + m - s0 + kBPad];
+                        if (k == 0 && j == 0) {  // m = 0: Ytilde_l^0 = Q / sqrt2
+                            ax = fmaf(Qx, gp, ax);
+                            ay = fmaf(Qy, gp, ay);
+                            az = fmaf(Qz, gp, az);
+                            if (NORM) S = fmaf(lf * (q * inv_sqrt2), gp, S);
+                        } else {
+                            const float gn = gb[ctr - m - s0 + kBPad];
+                            const float c = cm[k], sn = sm[k], c1 = cm1[k], s1 = sm1[k];
+                            const float A = fmaf(gp, c, gn * sn);     // g+ c_m + g- s_m
+                            const float B = fmaf(gp, c1, gn * s1);    // g+ c_{m-1} + g- s_{m-1}
+                            const float Cc = fmaf(gn, c1, -(gp * s1));  // g- c_{m-1} - g+ s_{m-1}
+                            const float mQ = (jf + float(kG * k)) * q;
+                            ax = fmaf(Qx, A, fmaf(mQ, B, ax));
+                            ay = fmaf(Qy, A, fmaf(mQ, Cc, ay));
+                            az = fmaf(Qz, A, az);
+                            if (NORM) S = fmaf(lf * q, A, S);
+                        }
+                    }
+                    q2[k] = q1[k];
+                    q1[k] = q;
+                }
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    ta[k] = na[k];
+                    tf[k] = nf[k];
+                }
+            }
+            fence_proxy_async_smem();  // this buffer is rewritten by the async proxy two windows on
+            __syncwarp();
+            l = lw;
+            lw = lwn;
+            buf ^= 1;
+        }
+        if (failed) break;
+        // reduce over the 8 lanes of the point
+#pragma unroll
+        for (int off = kG / 2; off > 0; off >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, off, kG);
+            ay += __shfl_xor_sync(0xffffffffu, ay, off, kG);
+            az += __shfl_xor_sync(0xffffffffu, az, off, kG);
+            if (NORM) S += __shfl_xor_sync(0xffffffffu, S, off, kG);
+        }
+        if (live && j == 0) {
+            if (NORM) {
+                ax = ir * fmaf(-x, S, ax);
+                ay = ir * fmaf(-y, S, ay);
+                az = ir * fmaf(-z, S, az);
+            }
+            dxyz[3 * p] = ax;
+            dxyz[3 * p + 1] = ay;
+            dxyz[3 * p + 2] = az;
+        }
+    }
+    if (pending && j == 0) {
+        // loads issued but not observed (after a timeout) may still be in
+        // flight: wait for them, bounded, before the shared memory goes away
+        for (int b = 0; b < 2; ++b)
+            if (pending & (1u << b)) (void)mbar_wait_bounded(&bars[b], (parity >> b) & 1u, kRowWaitPolls);
+    }
+    __syncwarp();
+}
+
 template <typename TO, bool GRAD, bool NORM, int NCH>
 int launch_row(const FwdArgs& a, const float* tb) {
     auto kern = row_fwd_kernel<TO, GRAD, NORM, NCH>;
@@ -331,6 +576,42 @@ int launch_row(const FwdArgs& a, const float* tb) {
     return int(cudaGetLastError());
 }
 
+template <bool NORM, int NCH>
+int launch_row_bwd(const BwdArgs& a, const float* tb) {
+    auto kern = row_bwd_kernel<NORM, NCH>;
+    const size_t per_warp = row_bwd_warp_bytes();
+    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : 2;
+    const size_t smem = size_t(W) * per_warp;
+    if (smem > size_t(max_smem_optin())) return int(cudaErrorInvalidConfiguration);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return int(e);
+    }
+    int bps = a.launch.blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(kern), 32 * W, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        bps = std::max(occ, 1);
+    }
+    const int64_t ntiles = (a.n + kPW - 1) / kPW;
+    const int64_t want = (ntiles + W - 1) / W;
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const float*>(a.xyz), static_cast<const float*>(a.g), a.n, a.l_max, tb,
+        float(host_tables().inv_sqrt2), static_cast<float*>(a.dxyz), a.status);
+    return int(cudaGetLastError());
+}
+
+template <int NCH>
+int launch_row_bwd_flags(const BwdArgs& a, const float* tb) {
+    return a.normalized ? launch_row_bwd<true, NCH>(a, tb) : launch_row_bwd<false, NCH>(a, tb);
+}
+
 template <typename TO, int NCH>
 int launch_row_flags(const FwdArgs& a, const float* tb) {
     const bool grad = a.dsph != nullptr, norm = a.normalized != 0;
@@ -347,6 +628,19 @@ int launch_row_out(const FwdArgs& a, const float* tb) {
 }  // namespace
 
 #if SPH_ROW_PART == 0
+int row_bwd_part0(const BwdArgs& a) {
+    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
+    if (!tb) return int(cudaErrorMemoryAllocation);
+    switch ((a.l_max + 1 + kG - 1) / kG) {
+        case 3:
+            return launch_row_bwd_flags<3>(a, tb);
+        case 4:
+            return launch_row_bwd_flags<4>(a, tb);
+        default:
+            return launch_row_bwd_flags<5>(a, tb);
+    }
+}
+
 int row_fwd_part0(const FwdArgs& a) {
     const float* tb = static_cast<const float*>(device_tables(SPH_F32));
     if (!tb) return int(cudaErrorMemoryAllocation);
@@ -360,6 +654,19 @@ int row_fwd_part0(const FwdArgs& a) {
     }
 }
 #else
+int row_bwd_part1(const BwdArgs& a) {
+    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
+    if (!tb) return int(cudaErrorMemoryAllocation);
+    switch ((a.l_max + 1 + kG - 1) / kG) {
+        case 6:
+            return launch_row_bwd_flags<6>(a, tb);
+        case 7:
+            return launch_row_bwd_flags<7>(a, tb);
+        default:
+            return launch_row_bwd_flags<8>(a, tb);
+    }
+}
+
 int row_fwd_part1(const FwdArgs& a) {
     const float* tb = static_cast<const float*>(device_tables(SPH_F32));
     if (!tb) return int(cudaErrorMemoryAllocation);

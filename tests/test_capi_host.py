@@ -191,14 +191,16 @@ def test_argument_errors_before_any_cuda_call():
         assert _err(C.sphericart_compute_ex, 16, 4, 30, 0, 0, 0, 0, k, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
         assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, k, launch, 16, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 6, launch, 16, none, none, none) == C.SPH_EINVAL
-    # ROW: FP32 arithmetic, 16 <= l_max <= 63, no Hessians, no backward
+    # ROW: FP32 arithmetic, 16 <= l_max <= 63, no Hessians; backward (FP32) but no double backward
     R = C.SPH_KERNEL_ROW
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 64, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 1, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 1, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 0, R, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
-    assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, R, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_backward, 16, 16, 4, 15, 0, 0, R, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 1, R, launch, 16, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_double_backward, 16, 16, 16, 4, 20, 0, 0, R, launch, 16, 16, none) == C.SPH_EUNSUPPORTED
     assert C.sphericart_max_l(C.SPH_F32, C.SPH_Q_NATIVE, R) == 63
     # NULL required pointers
     assert _err(C.sphericart_compute_ex, none, 4, 8, 0, 0, 0, 0, 0, launch, 16, none, none, none) == C.SPH_EINVAL

@@ -177,3 +177,64 @@ def test_sweep_workload_sampled(l_max):
     else:
         assert value_errors(v[idx], rv, p, l_max, True).max() < 1e-4
         assert grad_errors(g[idx], rg, p, l_max, True).max() < 1e-3
+
+
+# --------------------------------------------------------------- fused backward
+def _rel(got, ref):
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_backward_matches_oracle(normalized):
+    """dxyz = sum_k g_k dY_k/dx (recomputed recursion, g read by bulk-loaded
+    windows) vs the oracle's contraction, every channel count."""
+    n = 203
+    x = inputs.shell_points(n, 0.7, 3.0, seed=410).astype(np.float32).astype(np.float64)
+    xt = torch.from_numpy(x.astype(np.float32)).to(DEV)
+    for l_max in (16, 17, 20, 23, 24, 31, 32, 39, 40, 47, 48, 55, 56, 63):
+        K = (l_max + 1) ** 2
+        g = inputs.upstream(n, K, seed=411 + l_max).astype(np.float32)
+        dx = api.backward(xt, torch.from_numpy(g).to(DEV), l_max, normalized, kernel="row")
+        torch.cuda.synchronize()
+        ref = oracle.backward(x, g.astype(np.float64), l_max, normalized)
+        tol = 2e-5 if l_max <= 20 else 1e-4  # FP32 rounding accumulated over the recursion
+        assert _rel(dx.cpu().numpy(), ref) < tol, (l_max, _rel(dx.cpu().numpy(), ref))
+    assert api.device_status() == 0
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2, 3])
+def test_backward_unaligned_rows_and_ragged_tiles(offset):
+    """g rows starting at every 4-byte offset from a 16-byte boundary (bulk
+    loads of the aligned middle, plain loads of the edges), n not a multiple
+    of the 4 points a warp owns; AUTO picks ROW here and matches SLICE."""
+    n, l_max = 1001, 27
+    K = (l_max + 1) ** 2
+    x = torch.from_numpy(inputs.normal_points(n, seed=412).astype(np.float32)).to(DEV)
+    buf = torch.from_numpy(inputs.upstream(n * K + offset, 1, seed=413).astype(np.float32)[:, 0]).to(DEV)
+    g = buf[offset:].view(n, K)
+    for normalized in (False, True):
+        a = api.backward(x, g, l_max, normalized)  # AUTO
+        b = api.backward(x, g, l_max, normalized, kernel="slice")
+        torch.cuda.synchronize()
+        assert _rel(a.cpu().numpy(), b.double().cpu().numpy()) < 2e-5
+    assert api.device_status() == 0
+
+
+def test_backward_launch_shapes_identical():
+    n, l_max = 20_011, 33
+    K = (l_max + 1) ** 2
+    x = torch.from_numpy(inputs.normal_points(n, seed=414).astype(np.float32)).to(DEV)
+    g = torch.from_numpy(inputs.upstream(n, K, seed=415)).to(DEV)
+    base = None
+    for W in (1, 2, 4, 8):
+        for B in (0, 1):
+            d = api.backward(x, g, l_max, True, kernel="row", launch=C.make_launch(0, W, B, 0))
+            torch.cuda.synchronize()
+            if base is None:
+                base = d.clone()
+            else:
+                assert torch.equal(d, base)
+    p = x[::97].double().cpu().numpy()
+    ref = oracle.backward(p, g[::97].double().cpu().numpy(), l_max, True)
+    assert _rel(base[::97].cpu().numpy(), ref) < 1e-4
