@@ -25,40 +25,113 @@ struct ValVis {
     __device__ __forceinline__ void emit(int, int k, const Deriv<T>& d) { row[k] = d.v; }
 };
 
+constexpr int kExpBatch = 32;  // centres whose CSR offsets a warp holds in registers
+
 // Per-warp shared memory: Y rows of a 32-point chunk (odd stride), two
 // buffers of the chunk's radial rows in their global layout [e][n][l]
-// (filled by bulk copies one chunk ahead), the [n_rad, K] accumulator of the
-// current centre, and two mbarriers.
+// (filled by bulk copies one chunk ahead), the [n_rad, K] partial sums of a
+// centre that continues into the next chunk, the chunk's segment table (end
+// of each centre's points within the chunk, and the centre) and two mbarriers.
 template <int L, typename T>
 __host__ __device__ constexpr size_t expansion_warp_bytes(int nr) {
     constexpr int K = (L + 1) * (L + 1);
     constexpr int SY = (K % 2 == 0) ? K + 1 : K;
     const int RW = nr * (L + 1);
     return align16(size_t(32) * SY * sizeof(T)) + 2 * align16(size_t(32) * RW * sizeof(T)) +
-           align16(size_t(nr) * K * sizeof(T)) + 16;
+           align16(size_t(nr) * K * sizeof(T)) + align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))) + 16;
 }
 
-// The work of one warp is the sequence of (centre, 32-point chunk) items of
-// the centres i = first, first + stride, ...; `next_item` advances along it.
-struct ExpItem {
-    int64_t i;   // centre (>= ncent: done)
-    int64_t ch;  // first point of the chunk
-    int64_t e1;  // end of the centre's points
-    bool valid_centre;
+// CSR offsets of kExpBatch consecutive centres [base, base + 32) of a warp's
+// range, one centre per lane.
+struct ExpBatch {
+    int64_t base;
+    int64_t lo, hi;  // this lane's centre owns the points [lo, hi)
+    bool real;       // base + lane lies in the warp's centre range
+    bool ok;         // real and 0 <= lo <= hi <= n_points
 };
 
-__device__ __forceinline__ void first_chunk(ExpItem& it, const int64_t* __restrict__ offsets, int64_t ncent,
-                                            int64_t npts, int64_t stride) {
-    while (it.i < ncent) {
-        const int64_t e0 = offsets[it.i], e1 = offsets[it.i + 1];
-        it.valid_centre = !(e0 < 0 || e1 < e0 || e1 > npts);
-        it.ch = e0;
-        it.e1 = e1;
-        return;  // empty and malformed centres are items too (they write their output)
+__device__ __forceinline__ ExpBatch load_batch(const int64_t* __restrict__ offsets, int64_t base, int64_t ce,
+                                               int64_t npts, int lane) {
+    ExpBatch bt{base, 0, 0, false, false};
+    const int64_t ci = base + lane;
+    if (ci < ce) {
+        bt.real = true;
+        bt.lo = offsets[ci];
+        bt.hi = offsets[ci + 1];
+        bt.ok = bt.lo >= 0 && bt.lo <= bt.hi && bt.hi <= npts;
     }
-    (void)stride;
+    return bt;
 }
 
+// Position in a batch: the first centre not yet written out, whether its sums
+// so far are carried in shared memory, and the next point.
+struct ExpCursor {
+    int jc;
+    bool carry;
+    int64_t p;
+};
+
+// One chunk: up to 32 consecutive points [p, p + cnt) of a run of consecutive
+// well-formed centres (their point ranges abut), and the centres [j, jm) of
+// the batch that own them or end in them (empty centres included).
+struct ExpChunk {
+    int64_t p;
+    int cnt;
+    int j, jm;
+    bool carry_in;  // centre j was started by an earlier chunk
+    bool last_fin;  // centre jm - 1 ends in this chunk (else it continues)
+    bool valid;     // false: no unfinished well-formed centre left in the batch
+};
+
+// Warp-uniform: the chunk that starts at cursor `cu` of batch `bt`.
+__device__ __forceinline__ ExpChunk plan_chunk(const ExpBatch& bt, const ExpCursor& cu, int lane) {
+    ExpChunk ch{0, 0, 0, 0, false, false, false};
+    const unsigned vmask = __ballot_sync(0xffffffffu, bt.ok);
+    const unsigned avail = cu.jc < 32 ? vmask & (0xffffffffu << cu.jc) : 0u;
+    if (!avail) return ch;
+    ch.valid = true;
+    const int j = __ffs(avail) - 1;  // == cu.jc when carrying
+    ch.j = j;
+    ch.carry_in = cu.carry;
+    const int64_t loj = __shfl_sync(0xffffffffu, bt.lo, j);
+    ch.p = cu.carry ? cu.p : loj;
+    // the run ends before the first malformed (or absent) centre after j
+    const unsigned inv = ~vmask & (j < 31 ? (0xffffffffu << (j + 1)) : 0u);
+    const int k = inv ? __ffs(inv) - 1 : 32;
+    const int64_t run_hi = __shfl_sync(0xffffffffu, bt.hi, k - 1);
+    ch.cnt = int(min(int64_t(32), run_hi - ch.p));
+    const int64_t e = ch.p + ch.cnt;
+    // members: the centres of the run up to the first one with points past e
+    const unsigned nonmem = __ballot_sync(0xffffffffu, lane > j && lane < k && (bt.lo > e || (bt.lo == e && bt.hi > e)));
+    ch.jm = nonmem ? __ffs(nonmem) - 1 : k;
+    ch.last_fin = __shfl_sync(0xffffffffu, bt.hi, ch.jm - 1) <= e;
+    return ch;
+}
+
+__device__ __forceinline__ ExpCursor after_chunk(const ExpChunk& ch) {
+    return ch.last_fin ? ExpCursor{ch.jm, false, ch.p + ch.cnt} : ExpCursor{ch.jm - 1, true, ch.p + ch.cnt};
+}
+
+// Malformed centres of a batch: flag them and write zeros.
+template <typename T>
+__device__ __forceinline__ void zero_malformed(const ExpBatch& bt, T* __restrict__ c, int nout,
+                                               uint32_t* __restrict__ status, int lane) {
+    unsigned bad = __ballot_sync(0xffffffffu, bt.real && !bt.ok);
+    if (bad && lane == 0) atomicOr(status, kStatusBadOffsets);
+    while (bad) {
+        const int m = __ffs(bad) - 1;
+        bad &= bad - 1;
+        T* ci = c + (bt.base + m) * nout;
+        for (int o = lane; o < nout; o += 32) ci[o] = T(0);
+    }
+}
+
+// Each warp owns a contiguous range of centres and streams their points in
+// chunks of 32 that cross centre boundaries: a chunk's harmonics are computed
+// one point per lane, and each lane accumulates its (column, channel) items
+// over the chunk's segments, writing a centre's sums to global memory from
+// registers when the centre ends. The radial rows and coordinates of the next
+// chunk, and the offsets of the next 32 centres, are loaded one step ahead.
 template <int L, bool NORM, typename T>
 __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xyz, const T* __restrict__ R,
                                                         const int64_t* __restrict__ offsets, int64_t ncent,
@@ -76,18 +149,26 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     unsigned char* base = smem + size_t(warp) * expansion_warp_bytes<L, T>(nr);
     const size_t ybytes = align16(size_t(32) * SY * sizeof(T));
     const size_t rbytes = align16(size_t(32) * RW * sizeof(T));
+    const size_t cbytes = align16(size_t(nr) * K * sizeof(T));
     T* Ys = reinterpret_cast<T*>(base);
     T* Rb0 = reinterpret_cast<T*>(base + ybytes);
     T* Rb1 = reinterpret_cast<T*>(base + ybytes + rbytes);
     T* Cs = reinterpret_cast<T*>(base + ybytes + 2 * rbytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + 2 * rbytes + align16(size_t(nr) * K * sizeof(T)));
+    int64_t* seg_cid = reinterpret_cast<int64_t*>(base + ybytes + 2 * rbytes + cbytes);
+    int* seg_end = reinterpret_cast<int*>(seg_cid + kExpBatch);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + 2 * rbytes + cbytes +
+                                                align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))));
     const int nout = nr * K;
-    const int64_t stride = int64_t(gridDim.x) * W;
     const int NG = (nr + 3) / 4;  // radial channel groups of 4
     int col_groups = 0;           // sum over l of ceil((2l+1)/4)
 #pragma unroll
     for (int ll = 0; ll <= L; ++ll) col_groups += (2 * ll + 1 + 3) / 4;
     const int n_items = col_groups * NG;
+
+    // the warp's centres [cb, ce)
+    const int64_t G = int64_t(gridDim.x) * W;
+    const int64_t g = int64_t(blockIdx.x) * W + warp;
+    const int64_t cb = ncent * g / G, ce = ncent * (g + 1) / G;
 
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -98,74 +179,64 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     uint32_t phase = 0, pending = 0;
     bool failed = false;
 
-    // Issues the radial rows of chunk (ch, cnt) into buffer b: bulk copy of
-    // the whole rows when allowed, else nothing (loaded at use time).
-    auto issue = [&](int b, int64_t ch, int cnt) -> int64_t {
-        if (!bulk || cnt <= 0) return 0;
-        const uint32_t bytes = uint32_t(size_t(cnt) * RW * sizeof(T));
+    // Bulk copy of a chunk's radial rows into buffer b (when allowed).
+    auto issue = [&](int b, const ExpChunk& ch) {
+        if (!bulk || ch.cnt <= 0) return;
+        const uint32_t bytes = uint32_t(size_t(ch.cnt) * RW * sizeof(T));
         if (lane == 0) {
             mbar_arrive_expect_tx(&bar[b], bytes);
-            bulk_load(b ? Rb1 : Rb0, R + ch * RW, bytes, &bar[b]);
+            bulk_load(b ? Rb1 : Rb0, R + ch.p * RW, bytes, &bar[b]);
         }
         pending |= (1u << b);
-        return cnt;
+    };
+    auto coords = [&](const ExpChunk& ch, T& x, T& y, T& z) {
+        if (lane < ch.cnt) {
+            const int64_t p = ch.p + lane;
+            x = xyz[3 * p];
+            y = xyz[3 * p + 1];
+            z = xyz[3 * p + 2];
+        }
     };
 
-    ExpItem cur{int64_t(blockIdx.x) * W + warp, 0, 0, true};
-    first_chunk(cur, offsets, ncent, npts, stride);
+    ExpBatch cur = load_batch(offsets, cb, ce, npts, lane);
+    ExpBatch nxt = load_batch(offsets, cb + kExpBatch, ce, npts, lane);
+    zero_malformed(cur, c, nout, status, lane);
+    // the first chunk of the batch sequence from cursor cu (moving to later batches as needed)
+    auto next_chunk = [&](ExpCursor cu) -> ExpChunk {
+        ExpChunk ch = plan_chunk(cur, cu, lane);
+        while (!ch.valid && cur.base + kExpBatch < ce) {
+            cur = nxt;
+            nxt = load_batch(offsets, cur.base + kExpBatch, ce, npts, lane);
+            zero_malformed(cur, c, nout, status, lane);
+            ch = plan_chunk(cur, ExpCursor{0, false, 0}, lane);
+        }
+        return ch;
+    };
+
+    ExpChunk ch = next_chunk(ExpCursor{0, false, 0});
     int b = 0;
-    if (cur.i < ncent && cur.valid_centre) issue(0, cur.ch, int(min(int64_t(32), cur.e1 - cur.ch)));
     T px = T(0), py = T(0), pz = T(0);  // this lane's coordinates for the current chunk
-    if (cur.i < ncent && cur.valid_centre && cur.ch + lane < cur.e1) {
-        const int64_t p = cur.ch + lane;
-        px = xyz[3 * p];
-        py = xyz[3 * p + 1];
-        pz = xyz[3 * p + 2];
+    if (ch.valid) {
+        issue(0, ch);
+        coords(ch, px, py, pz);
     }
-    bool new_centre = true;
-    while (cur.i < ncent) {
-        T* ci = c + cur.i * nout;
-        if (!cur.valid_centre) {  // malformed CSR: flag it, write zeros, move on
-            if (lane == 0) atomicOr(status, kStatusBadOffsets);
-            for (int o = lane; o < nout; o += 32) ci[o] = T(0);
-            cur.i += stride;
-            first_chunk(cur, offsets, ncent, npts, stride);
-            if (cur.i < ncent && cur.valid_centre) {
-                issue(b, cur.ch, int(min(int64_t(32), cur.e1 - cur.ch)));
-                if (cur.ch + lane < cur.e1) {
-                    const int64_t p = cur.ch + lane;
-                    px = xyz[3 * p];
-                    py = xyz[3 * p + 1];
-                    pz = xyz[3 * p + 2];
-                }
-            }
-            new_centre = true;
-            continue;
+    while (ch.valid) {
+        // segment table of this chunk (before `cur` may move to the next batch)
+        if (lane >= ch.j && lane < ch.jm) {
+            seg_end[lane - ch.j] = int(min(cur.hi, ch.p + ch.cnt) - ch.p);
+            seg_cid[lane - ch.j] = cur.base + lane;
         }
-        if (new_centre) {
-            for (int o = lane; o < nout; o += 32) Cs[o] = T(0);
-            new_centre = false;
-        }
-        const int cnt = int(min(int64_t(32), cur.e1 - cur.ch));
-        // the next item: the centre's next chunk, else the next centre's first
-        ExpItem nx = cur;
-        nx.ch = cur.ch + 32;
-        bool nx_new_centre = false;
-        if (nx.ch >= cur.e1) {
-            nx.i = cur.i + stride;
-            first_chunk(nx, offsets, ncent, npts, stride);
-            nx_new_centre = true;
-        }
+        const int nseg = ch.jm - ch.j;
+        const int cnt = ch.cnt;
+        const bool carry_in = ch.carry_in, last_fin = ch.last_fin;
+        const int64_t p0 = ch.p;
+        // the next chunk: its radial rows and coordinates are loaded during this one
+        const ExpChunk nch = next_chunk(after_chunk(ch));
         const int nb = b ^ 1;
         T nxx = T(0), nxy = T(0), nxz = T(0);
-        if (nx.i < ncent && nx.valid_centre && !failed) {
-            issue(nb, nx.ch, int(min(int64_t(32), nx.e1 - nx.ch)));
-            if (nx.ch + lane < nx.e1) {
-                const int64_t p = nx.ch + lane;
-                nxx = xyz[3 * p];
-                nxy = xyz[3 * p + 1];
-                nxz = xyz[3 * p + 2];
-            }
+        if (nch.valid && !failed) {
+            issue(nb, nch);
+            coords(nch, nxx, nxy, nxz);
         }
         // harmonics of this chunk, one point per lane
         if (lane < cnt) {
@@ -191,16 +262,16 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                 failed = true;
                 break;
             }
-        } else {
-            const T* src = R + cur.ch * RW;
+        } else if (!bulk) {
+            const T* src = R + p0 * RW;
             for (int t = lane; t < cnt * RW; t += 32) Rs[t] = src[t];
         }
         __syncwarp();
         // Contraction, register-blocked: a work item is up to 4 columns of one
         // l block x 4 radial channels (16 accumulators); items are ordered by
-        // (l, column group, channel group) and dealt to lanes round-robin.
-        // Out-of-range columns/channels of an item read a valid entry and are
-        // masked at the write-back, so the inner loop has no predicates.
+        // (l, column group, channel group) and dealt to lanes round-robin, so a
+        // lane owns the same items in every chunk. Out-of-range columns and
+        // channels of an item read a valid entry and are masked at the writes.
         for (int it = lane; it < n_items; it += 32) {
             int l = 0, acc_items = 0;
             for (int ll = 0; ll <= L; ++ll) {  // decode the item
@@ -216,44 +287,59 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             const int n0 = (r - cg * NG) * 4;
             const int c0 = l * l + cg * 4;
             const int nc = min(4, 2 * l + 1 - cg * 4);
-            int col[4], rof[4];
+            int col[4], rof[4], cof[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) col[j] = c0 + min(j, nc - 1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) rof[q] = min(n0 + q, nr - 1) * RL + l;
+            for (int q = 0; q < 4; ++q) {
+                rof[q] = min(n0 + q, nr - 1) * RL + l;
+                cof[q] = min(n0 + q, nr - 1) * K;
+            }
             T acc[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[j][q] = Cs[min(n0 + q, nr - 1) * K + col[j]];
+                for (int q = 0; q < 4; ++q) acc[j][q] = carry_in ? Cs[cof[q] + col[j]] : T(0);
+            int s = 0;
+            for (int si = 0; si < nseg; ++si) {
+                const int se = seg_end[si];
 #pragma unroll 2
-            for (int e = 0; e < cnt; ++e) {
-                const T* ye = Ys + e * SY;
-                const T* re = Rs + e * RW;
-                T yv[4], rv[4];
+                for (int e = s; e < se; ++e) {
+                    const T* ye = Ys + e * SY;
+                    const T* re = Rs + e * RW;
+                    T yv[4], rv[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) yv[j] = ye[col[j]];
+                    for (int j = 0; j < 4; ++j) yv[j] = ye[col[j]];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) rv[q] = re[rof[q]];
+                    for (int q = 0; q < 4; ++q) rv[q] = re[rof[q]];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[j][q] += yv[j] * rv[q];
+                }
+                s = se;
+                if (si + 1 < nseg || last_fin) {  // the centre ends here: write it out
+                    T* ci = c + seg_cid[si] * nout;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (j < nc && n0 + q < nr) ci[cof[q] + col[j]] = acc[j][q];
+                            acc[j][q] = T(0);
+                        }
+                }
+            }
+            if (!last_fin) {  // carried into the next chunk
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[j][q] += yv[j] * rv[q];
+                    for (int q = 0; q < 4; ++q)
+                        if (j < nc && n0 + q < nr) Cs[cof[q] + col[j]] = acc[j][q];
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j < nc && n0 + q < nr) Cs[(n0 + q) * K + col[j]] = acc[j][q];
         }
         fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
         __syncwarp();
-        if (nx_new_centre) {  // centre finished: write it out
-            for (int o = lane; o < nout; o += 32) ci[o] = Cs[o];
-            __syncwarp();
-            new_centre = true;
-        }
-        cur = nx;
+        ch = nch;
         b = nb;
         px = nxx;
         py = nxy;
@@ -282,11 +368,19 @@ struct ExpArgs {
     uint32_t* status;
 };
 
+// Launches with up to a.warps warps per block, fewer when the per-warp staging
+// does not fit the opt-in shared-memory limit; kExpTooBig when one warp's does not.
+constexpr int kExpTooBig = -1;
+
 template <int L, bool NORM, typename T>
 int launch_expansion(const ExpArgs& a) {
     static const PointTabs<L, T, false> tb = make_point_tabs<L, T, false>();
-    const int W = a.warps;
-    const size_t smem = size_t(W) * expansion_warp_bytes<L, T>(a.nr);
+    const size_t per_warp = expansion_warp_bytes<L, T>(a.nr);
+    const size_t limit = size_t(max_smem_optin());
+    if (per_warp > limit) return kExpTooBig;
+    int W = a.warps;
+    while (W > 1 && size_t(W) * per_warp > limit) --W;
+    const size_t smem = size_t(W) * per_warp;
     auto kern = expansion_kernel<L, NORM, T>;
     cudaError_t err = ensure_smem(kern, smem);
     if (err != cudaSuccess) return int(err);
@@ -367,16 +461,12 @@ extern "C" int sphericart_expansion(const void* xyz, const void* radial, const i
     }
     ExpArgs a{xyz, radial, offsets, n_centres, n_points, n_rad, l_max, normalized ? 1 : 0, dtype, c, stream, 4,
               status};
-    // Fit the per-warp staging (Y rows, R rows, accumulators) in the opt-in limit.
-    const size_t K = size_t(l_max + 1) * (l_max + 1);
-    const size_t per_warp = e * (32 * (K + 1) + 2 * 32 * size_t(n_rad) * (l_max + 1) + size_t(n_rad) * K) + 80;
-    while (a.warps > 1 && size_t(a.warps) * per_warp > size_t(max_smem_optin())) --a.warps;
-    if (per_warp > size_t(max_smem_optin())) {
-        set_error("expansion: n_rad=%d with l_max=%d needs %zu bytes of shared memory per warp", n_rad, l_max,
-                  per_warp);
+    const int err = launch_expansion_any(a);
+    if (err == kExpTooBig) {
+        set_error("expansion: n_rad=%d with l_max=%d needs more shared memory per warp than the device has", n_rad,
+                  l_max);
         return SPH_EUNSUPPORTED;
     }
-    const int err = launch_expansion_any(a);
     if (err) {
         set_error("expansion launch: %s", cudaGetErrorString(static_cast<cudaError_t>(err)));
         return SPH_ECUDA;

@@ -88,3 +88,47 @@ def test_expansion_malformed_offsets_flagged_without_fault():
     assert np.all(cc[2] == 0) and np.all(cc[6] == 0) and np.all(cc[7] == 0)
     assert np.any(cc[0] != 0)
     assert api.device_status() == 0  # read-and-clear
+
+
+@pytest.mark.parametrize("l_max,nr,dtype", [(3, 5, torch.float32), (2, 3, torch.float32), (6, 8, torch.float64)])
+def test_expansion_many_centres_per_warp(l_max, nr, dtype):
+    """150,000 centres of mixed sizes (empty, a few points, around one and two
+    32-point chunks), so that every warp streams several batches of 32
+    centres whose points cross chunk boundaries, with a few malformed centres
+    in between. The oracle checks a prefix of 4,000 centres (whole warp
+    ranges), 300 sampled centres and the centres next to the malformed ones.
+    (l_max 2 with 3 channels has 36-byte radial rows: the plain-load path.)"""
+    rng = np.random.default_rng(630 + l_max)
+    ncent = 150_000
+    counts = rng.choice([0, 0, 1, 1, 2, 3, 5, 31, 33, 64], size=ncent)
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    E = int(offs[-1])
+    bad = offs.copy()
+    for i in (17, 70_011, 149_999):  # centre i-1 decreasing; centre i starts one point early
+        bad[i] = bad[i - 1] - 1
+    xyz = inputs.shell_points(E, 0.7, 5.0, seed=631)
+    R = inputs.upstream(E, nr * (l_max + 1), seed=632).reshape(E, nr, l_max + 1)
+    npd = np.float32 if dtype == torch.float32 else np.float64
+    xyz, R = xyz.astype(npd), R.astype(npd)
+    c = api.expansion(torch.from_numpy(xyz).to(DEV), torch.from_numpy(R).to(DEV), torch.from_numpy(bad).to(DEV),
+                      l_max)
+    torch.cuda.synchronize()
+    assert api.device_status() & 2
+    cc = c.double().cpu().numpy()
+    ok = (bad[:-1] >= 0) & (bad[:-1] <= bad[1:]) & (bad[1:] <= E)
+    assert (~ok).sum() == 3 and np.all(cc[~ok] == 0)
+    tol = 2e-6 if dtype == torch.float32 else 1e-13
+    x64, R64 = xyz.astype(np.float64), R.astype(np.float64)
+    n0 = 4000
+    ref = oracle.expansion(x64[: bad[n0]], R64[: bad[n0]], bad[: n0 + 1], l_max)
+    err = np.abs(cc[:n0] - ref) / _scale(x64[: bad[n0]], R64[: bad[n0]], bad[: n0 + 1], l_max, False)
+    assert err.max() < tol, err.max()
+    sample = np.concatenate([rng.choice(ncent, 300, replace=False), [70_009, 70_011, 70_012, 149_999]])
+    for i in sample:
+        if not ok[i]:
+            continue
+        a, b = bad[i], bad[i + 1]
+        one = np.array([0, b - a])
+        ref = oracle.expansion(x64[a:b], R64[a:b], one, l_max)[0]
+        sc = _scale(x64[a:b], R64[a:b], one, l_max, False)[0]
+        assert (np.abs(cc[i] - ref) / sc).max() < tol, i
