@@ -19,15 +19,50 @@ namespace sph {
 constexpr uint32_t kStatusBadOffsets = 2u;
 constexpr int kExpansionMaxRad = 64;
 
-template <typename T, int K>
+// Row layout of the staged harmonics: the 2l+1 columns of degree l in groups
+// of 4 slots (the last group of a degree padded with zeros), group g at word
+// 4g + floor(g / 8). The lanes of one contraction round read up to 32
+// consecutive groups at the same slot; without the skew of one word per block
+// of 8 groups, groups 8 apart would share a bank. With it, 4d + (1 or 2 or 3)
+// for groups d < 32 apart is never a multiple of 32 words, so the reads are
+// free of bank conflicts, and each lane reads its 4 slots at immediate offsets.
+__host__ __device__ constexpr int exp_gstart(int l) { return l == 0 ? 0 : l + (l - 1) * (l - 1) / 4; }
+__host__ __device__ constexpr int exp_gbase(int g) { return 4 * g + g / 8; }
+__host__ __device__ constexpr int exp_ypos(int l, int k) {
+    return exp_gbase(exp_gstart(l) + (k - l * l) / 4) + (k - l * l) % 4;
+}
+// Row stride in words: odd, so that the lanes' stores (one row each) are
+// conflict-free too.
+template <int L>
+__host__ __device__ constexpr int exp_row_words() {
+    return (exp_gbase(exp_gstart(L + 1) - 1) + 4) | 1;
+}
+
+// Every column gets its own word inside the row, for every supported l_max.
+constexpr bool exp_layout_ok() {
+    for (int L = 0; L <= 16; ++L) {
+        const int SY = (exp_gbase(exp_gstart(L + 1) - 1) + 4) | 1;
+        int prev = -1;
+        for (int l = 0; l <= L; ++l)
+            for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
+                if (exp_ypos(l, k) <= prev) return false;
+                prev = exp_ypos(l, k);
+            }
+        if (prev + 1 >= SY || exp_gbase(exp_gstart(L + 1) - 1) + 3 >= SY) return false;
+    }
+    return true;
+}
+static_assert(exp_layout_ok(), "grouped Y layout must be injective and inside the row");
+
+template <typename T>
 struct ValVis {
     T* row;
-    __device__ __forceinline__ void emit(int, int k, const Deriv<T>& d) { row[k] = d.v; }
+    __device__ __forceinline__ void emit(int l, int k, const Deriv<T>& d) { row[exp_ypos(l, k)] = d.v; }
 };
 
 constexpr int kExpBatch = 32;  // centres whose CSR offsets a warp holds in registers
 
-// Per-warp shared memory: Y rows of a 32-point chunk (odd stride), two
+// Per-warp shared memory: Y rows of a 32-point chunk (grouped layout), two
 // buffers of the chunk's radial rows in their global layout [e][n][l]
 // (filled by bulk copies one chunk ahead), the [n_rad, K] partial sums of a
 // centre that continues into the next chunk, the chunk's segment table (end
@@ -35,10 +70,12 @@ constexpr int kExpBatch = 32;  // centres whose CSR offsets a warp holds in regi
 template <int L, typename T>
 __host__ __device__ constexpr size_t expansion_warp_bytes(int nr) {
     constexpr int K = (L + 1) * (L + 1);
-    constexpr int SY = (K % 2 == 0) ? K + 1 : K;
     const int RW = nr * (L + 1);
-    return align16(size_t(32) * SY * sizeof(T)) + 2 * align16(size_t(32) * RW * sizeof(T)) +
-           align16(size_t(nr) * K * sizeof(T)) + align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))) + 16;
+    // radial buffers: 32 rows plus 3 rows' worth of channels that the masked
+    // channels of the last row's items read past its end
+    return align16(size_t(32) * exp_row_words<L>() * sizeof(T)) +
+           2 * align16((size_t(32) * RW + 3 * (L + 1)) * sizeof(T)) + align16(size_t(nr) * K * sizeof(T)) +
+           align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))) + 16;
 }
 
 // CSR offsets of kExpBatch consecutive centres [base, base + 32) of a warp's
@@ -139,7 +176,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                                                         const __grid_constant__ PointTabs<L, T, false> tb,
                                                         T* __restrict__ c, uint32_t* __restrict__ status, int bulk) {
     constexpr int K = (L + 1) * (L + 1);
-    constexpr int SY = (K % 2 == 0) ? K + 1 : K;
+    constexpr int SY = exp_row_words<L>();
     constexpr int RL = L + 1;
     const int RW = nr * RL;  // radial row width ([n][l])
     extern __shared__ __align__(128) unsigned char smem[];
@@ -148,7 +185,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     const int W = blockDim.x >> 5;
     unsigned char* base = smem + size_t(warp) * expansion_warp_bytes<L, T>(nr);
     const size_t ybytes = align16(size_t(32) * SY * sizeof(T));
-    const size_t rbytes = align16(size_t(32) * RW * sizeof(T));
+    const size_t rbytes = align16((size_t(32) * RW + 3 * RL) * sizeof(T));
     const size_t cbytes = align16(size_t(nr) * K * sizeof(T));
     T* Ys = reinterpret_cast<T*>(base);
     T* Rb0 = reinterpret_cast<T*>(base + ybytes);
@@ -174,6 +211,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
     }
+    for (int t = lane; t < 32 * SY; t += 32) Ys[t] = T(0);  // padding slots stay zero
     fence_proxy_async_smem();
     __syncwarp();
     uint32_t phase = 0, pending = 0;
@@ -246,7 +284,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             } else {
                 r2 = x * x + y * y + z * z;
             }
-            ValVis<T, K> vis{Ys + size_t(lane) * SY};
+            ValVis<T> vis{Ys + size_t(lane) * SY};
             point_core<L, false, false>(x, y, z, r2, tb, vis);
         }
         T* const Rs = b ? Rb1 : Rb0;
@@ -267,11 +305,13 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             for (int t = lane; t < cnt * RW; t += 32) Rs[t] = src[t];
         }
         __syncwarp();
-        // Contraction, register-blocked: a work item is up to 4 columns of one
-        // l block x 4 radial channels (16 accumulators); items are ordered by
-        // (l, column group, channel group) and dealt to lanes round-robin, so a
-        // lane owns the same items in every chunk. Out-of-range columns and
-        // channels of an item read a valid entry and are masked at the writes.
+        // Contraction, register-blocked: a work item is one group of 4 columns
+        // of an l block x 4 radial channels (16 accumulators); items are
+        // ordered by (l, column group, channel group) and dealt to lanes
+        // round-robin, so a lane owns the same items in every chunk. A lane
+        // reads its 4 columns and 4 channels at immediate offsets from one
+        // pointer each: padding slots (zero) and channels past n_rad (the next
+        // row, or the buffer's tail) feed accumulators masked at the writes.
         for (int it = lane; it < n_items; it += 32) {
             int l = 0, acc_items = 0;
             for (int ll = 0; ll <= L; ++ll) {  // decode the item
@@ -287,44 +327,41 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             const int n0 = (r - cg * NG) * 4;
             const int c0 = l * l + cg * 4;
             const int nc = min(4, 2 * l + 1 - cg * 4);
-            int col[4], rof[4], cof[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) col[j] = c0 + min(j, nc - 1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                rof[q] = min(n0 + q, nr - 1) * RL + l;
-                cof[q] = min(n0 + q, nr - 1) * K;
-            }
+            const int nq = min(4, nr - n0);
+            const T* yp = Ys + exp_gbase(exp_gstart(l) + cg);
+            const T* rp = Rs + n0 * RL + l;
+            const int cbase = n0 * K + c0;  // [n][K] offset of the item's first output
             T acc[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[j][q] = carry_in ? Cs[cof[q] + col[j]] : T(0);
+                for (int q = 0; q < 4; ++q)
+                    acc[j][q] = (carry_in && j < nc && q < nq) ? Cs[cbase + q * K + j] : T(0);
             int s = 0;
             for (int si = 0; si < nseg; ++si) {
                 const int se = seg_end[si];
-#pragma unroll 2
+#pragma unroll 4
                 for (int e = s; e < se; ++e) {
-                    const T* ye = Ys + e * SY;
-                    const T* re = Rs + e * RW;
+                    const T* ye = yp + e * SY;
+                    const T* re = rp + e * RW;
                     T yv[4], rv[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) yv[j] = ye[col[j]];
+                    for (int j = 0; j < 4; ++j) yv[j] = ye[j];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) rv[q] = re[rof[q]];
+                    for (int q = 0; q < 4; ++q) rv[q] = re[q * RL];
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[j][q] += yv[j] * rv[q];
+                        for (int q = 0; q < 4; ++q) acc[j][q] = fma(yv[j], rv[q], acc[j][q]);
                 }
                 s = se;
                 if (si + 1 < nseg || last_fin) {  // the centre ends here: write it out
-                    T* ci = c + seg_cid[si] * nout;
+                    T* ci = c + seg_cid[si] * nout + cbase;
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            if (j < nc && n0 + q < nr) ci[cof[q] + col[j]] = acc[j][q];
+                            if (j < nc && q < nq) ci[q * K + j] = acc[j][q];
                             acc[j][q] = T(0);
                         }
                 }
@@ -334,7 +371,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (j < nc && n0 + q < nr) Cs[cof[q] + col[j]] = acc[j][q];
+                        if (j < nc && q < nq) Cs[cbase + q * K + j] = acc[j][q];
             }
         }
         fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
