@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sph_point.cuh"
 
@@ -312,6 +313,9 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
         // reads its 4 columns and 4 channels at immediate offsets from one
         // pointer each: padding slots (zero) and channels past n_rad (the next
         // row, or the buffer's tail) feed accumulators masked at the writes.
+        // With 2 or 4 channel groups, group g holds the channels g + NG q: the
+        // words a round reads for one q are then NG (l_max+1) consecutive
+        // ones, not NG runs 4 (l_max+1) apart that wrap around the banks.
         for (int it = lane; it < n_items; it += 32) {
             int l = 0, acc_items = 0;
             for (int ll = 0; ll <= L; ++ll) {  // decode the item
@@ -324,54 +328,71 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
             }
             const int r = it - acc_items;
             const int cg = r / NG;
-            const int n0 = (r - cg * NG) * 4;
+            const int ng = r - cg * NG;
+            const bool strided = NG == 2 || NG == 4;
+            const int nbase = strided ? ng : 4 * ng;  // channel of slot q: nbase + nstep q
+            const int nstep = strided ? NG : 1;
             const int c0 = l * l + cg * 4;
             const int nc = min(4, 2 * l + 1 - cg * 4);
-            const int nq = min(4, nr - n0);
+            bool qok[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) qok[q] = nbase + nstep * q < nr;
             const T* yp = Ys + exp_gbase(exp_gstart(l) + cg);
-            const T* rp = Rs + n0 * RL + l;
-            const int cbase = n0 * K + c0;  // [n][K] offset of the item's first output
+            const T* rp = Rs + nbase * RL + l;
+            const int cbase = nbase * K + c0;  // [n][K] offset of the item's first output
+            const int cstep = nstep * K;
             T acc[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    acc[j][q] = (carry_in && j < nc && q < nq) ? Cs[cbase + q * K + j] : T(0);
-            int s = 0;
-            for (int si = 0; si < nseg; ++si) {
-                const int se = seg_end[si];
+                    acc[j][q] = (carry_in && j < nc && qok[q]) ? Cs[cbase + q * cstep + j] : T(0);
+            // the segments of the chunk; S = channel stride of the item's slots
+            auto segments = [&](auto s_tag) {
+                constexpr int S = decltype(s_tag)::value;
+                int s = 0;
+                for (int si = 0; si < nseg; ++si) {
+                    const int se = seg_end[si];
 #pragma unroll 4
-                for (int e = s; e < se; ++e) {
-                    const T* ye = yp + e * SY;
-                    const T* re = rp + e * RW;
-                    T yv[4], rv[4];
+                    for (int e = s; e < se; ++e) {
+                        const T* ye = yp + e * SY;
+                        const T* re = rp + e * RW;
+                        T yv[4], rv[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) yv[j] = ye[j];
+                        for (int j = 0; j < 4; ++j) yv[j] = ye[j];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) rv[q] = re[q * RL];
+                        for (int q = 0; q < 4; ++q) rv[q] = re[q * S * RL];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                        for (int j = 0; j < 4; ++j)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[j][q] = fma(yv[j], rv[q], acc[j][q]);
+                            for (int q = 0; q < 4; ++q) acc[j][q] = fma(yv[j], rv[q], acc[j][q]);
+                    }
+                    s = se;
+                    if (si + 1 < nseg || last_fin) {  // the centre ends here: write it out
+                        T* ci = c + seg_cid[si] * nout + cbase;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (j < nc && qok[q]) ci[q * cstep + j] = acc[j][q];
+                                acc[j][q] = T(0);
+                            }
+                    }
                 }
-                s = se;
-                if (si + 1 < nseg || last_fin) {  // the centre ends here: write it out
-                    T* ci = c + seg_cid[si] * nout + cbase;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (j < nc && q < nq) ci[q * K + j] = acc[j][q];
-                            acc[j][q] = T(0);
-                        }
-                }
+            };
+            if (NG == 2) {
+                segments(std::integral_constant<int, 2>{});
+            } else if (NG == 4) {
+                segments(std::integral_constant<int, 4>{});
+            } else {
+                segments(std::integral_constant<int, 1>{});
             }
             if (!last_fin) {  // carried into the next chunk
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (j < nc && q < nq) Cs[cbase + q * K + j] = acc[j][q];
+                        if (j < nc && qok[q]) Cs[cbase + q * cstep + j] = acc[j][q];
             }
         }
         fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
