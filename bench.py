@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess"],
+        choices=["fwd", "fwd64", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     args = ap.parse_args()
@@ -461,7 +461,7 @@ def run_profile(args):
         _build.build()
     dev = torch.device("cuda", 0)
     n = args.n
-    if args.profile in ("fwd", "batch", "hess"):
+    if args.profile in ("fwd", "fwd64", "batch", "hess"):
         L = L_MAX
     elif args.profile in ("slice20", "degree20", "row20"):
         L = 20
@@ -473,6 +473,9 @@ def run_profile(args):
         sph = torch.empty((n, K), device=dev)
         dsph = torch.empty((n, 3, K), device=dev)
         fn = lambda: api.spherical_harmonics(x, L, False, gradients=True, out=(sph, dsph))  # noqa: E731
+    elif args.profile == "fwd64":
+        x64 = x.double()
+        fn = lambda: api.spherical_harmonics(x64, L, False, gradients=True)  # noqa: E731
     elif args.profile == "slice20":
         fn = lambda: api.spherical_harmonics(x, L, True, gradients=True, kernel="slice")  # noqa: E731
     elif args.profile == "degree20":
@@ -787,6 +790,14 @@ def run_extras(torch, np, api, inputs, dev, stream, n, L, K, sph, dsph, flush):
     del sb, db, gb, vb, xb, dx, dx_plain
     out["batch"] = run_batch_leg(torch, np, api, inputs, dev, stream, flush)
     out["expansion"] = run_expansion_leg(torch, np, api, inputs, dev, stream, flush)
+    from paper_2302_08381_gb300 import _capi as C
+
+    out["arith_peaks"] = {
+        "fp32_tflops": C.sphericart_fma_peak(C.SPH_F32, stream.cuda_stream, 3),
+        "fp64_tflops": C.sphericart_fma_peak(C.SPH_F64, stream.cuda_stream, 3),
+        "method": "sphericart_fma_peak: 8 independent FMA chains per thread, 64 warps per SM, best of 3 runs "
+        "of ~5 ms (2 flops per FMA)",
+    }
     bwd_bytes = BWD_N * (12 + Kb * 4 + 12)
     dbwd_bytes = BWD_N * (12 + Kb * 4 + 12 + Kb * 4 + 12)
     out["backward"] = {

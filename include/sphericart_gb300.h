@@ -369,6 +369,15 @@ int sphericart_tune_export(char* buf, size_t len, size_t* needed);
  * the current device (others are skipped); *imported receives the count. */
 int sphericart_tune_import(const char* text, int* imported);
 
+/* sphericart_fma_peak: measures this device's fused multiply-add throughput
+ * in `dtype` (SPH_F32 or SPH_F64): eight independent FMA chains per thread, 64
+ * warps per SM, ~5 ms per run, the best of `reps` runs timed with CUDA events
+ * on `stream` (synchronises). Writes TFLOP/s (2 flops per FMA) to *tflops
+ * (host memory): the arithmetic ceiling of kernels bound by that pipe.
+ * Returns SPH_EINVAL for another dtype, reps < 1 or NULL tflops, SPH_ECUDA
+ * without a usable device. */
+int sphericart_fma_peak(int dtype, void* stream, int reps, double* tflops);
+
 /* sphericart_version: library version as 10000*major + 100*minor + patch. */
 int sphericart_version(void);
 

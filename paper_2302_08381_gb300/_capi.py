@@ -97,6 +97,7 @@ _PROTOS = {
     ),
     "sphericart_tune_export": (_I, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "sphericart_tune_import": (_I, [ctypes.c_char_p, ctypes.POINTER(_I)]),
+    "sphericart_fma_peak": (_I, [_I, _P, _I, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -226,6 +227,12 @@ def sphericart_tune_import(text: str) -> int:
     k = ctypes.c_int(0)
     _call("sphericart_tune_import", text.encode(), ctypes.byref(k))
     return int(k.value)
+
+
+def sphericart_fma_peak(dtype, stream, reps=3) -> float:
+    v = ctypes.c_double(0)
+    _call("sphericart_fma_peak", dtype, stream, reps, ctypes.byref(v))
+    return float(v.value)
 
 
 def make_launch(points_per_tile=0, warps_per_block=0, blocks_per_sm=0, lanes_per_point=0):

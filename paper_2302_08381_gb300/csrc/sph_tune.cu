@@ -1,7 +1,8 @@
 // Autotuner for the POINT forward launch shape (points per tile, warps per
 // block, resident blocks per SM) and for ragged batch plans, timed on the
-// caller's own buffers with CUDA events; plus a text export/import of the
-// tuned table keyed by GPU name.
+// caller's own buffers with CUDA events; a text export/import of the tuned
+// table keyed by GPU name; and a measurement of the FP32 / FP64 FMA
+// throughput (the arithmetic ceiling of the kernels bound by those pipes).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,9 +56,84 @@ std::string device_name() {
     return s;
 }
 
+__device__ float g_fma_sink_f;
+__device__ double g_fma_sink_d;
+
+// Eight independent FMA chains per thread (a <- a b + c converges to
+// c / (1 - b), no denormals); the result is stored only under a condition that
+// never holds, which keeps every chain live.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters) {
+    constexpr int kChains = 8;
+    T a[kChains];
+    const T b = T(0.9999), c = T(1e-4);
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = T(threadIdx.x + i) * T(1e-3);
+#pragma unroll 16
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], b, c);
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += a[i];
+    if (s == T(-1)) {
+        if constexpr (sizeof(T) == 4) {
+            g_fma_sink_f = s;
+        } else {
+            g_fma_sink_d = s;
+        }
+    }
+}
+
+template <typename T>
+int fma_peak(cudaStream_t st, int reps, double* tflops) {
+    const int threads = 256;
+    const int blocks = 8 * sm_count();  // 64 warps per SM
+    EventPair ev;
+    auto run = [&](int iters, float* ms) -> bool {
+        cudaEventRecord(ev.a, st);
+        fma_peak_kernel<T><<<blocks, threads, 0, st>>>(iters);
+        cudaEventRecord(ev.b, st);
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) return false;
+        return cudaEventElapsedTime(ms, ev.a, ev.b) == cudaSuccess;
+    };
+    // calibrate the length to ~5 ms per run
+    int iters = 256;
+    float ms = 0.f;
+    if (!run(iters, &ms)) return SPH_ECUDA;
+    iters = int(std::min(double(1 << 24), std::max(256.0, iters * 5.0 / std::max(ms, 1e-3f))));
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        if (!run(iters, &ms)) return SPH_ECUDA;
+        best = std::min(best, ms);
+    }
+    const double flops = 2.0 * 8.0 * double(iters) * double(blocks) * threads;
+    *tflops = flops / (double(best) * 1e-3) / 1e12;
+    return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int sphericart_fma_peak(int dtype, void* stream, int reps, double* tflops) {
+    if ((dtype != SPH_F32 && dtype != SPH_F64) || reps < 1 || !tflops) {
+        set_error("fma_peak: dtype must be SPH_F32 or SPH_F64, reps >= 1, tflops non-NULL");
+        return SPH_EINVAL;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("fma_peak: no usable CUDA device");
+        return SPH_ECUDA;
+    }
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = dtype == SPH_F64 ? fma_peak<double>(st, reps, tflops) : fma_peak<float>(st, reps, tflops);
+    if (rc != SPH_OK) {
+        set_error("fma_peak: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return rc;
+}
 
 int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, int dtype, int out, void* sph,
                         void* dsph, void* stream, int reps, sph_launch* best, float* best_ms) {

@@ -260,3 +260,8 @@ def test_product_path_has_no_cpu_fallback():
         if name.endswith(".py"):
             text = open(os.path.join(src_dir, name)).read()
             assert "import oracle" not in text and "from oracle" not in text, name
+
+
+def test_fma_peak_argument_errors():
+    assert _err(C.sphericart_fma_peak, 7, None, 3) == C.SPH_EINVAL
+    assert _err(C.sphericart_fma_peak, C.SPH_F32, None, 0) == C.SPH_EINVAL

@@ -71,3 +71,14 @@ def test_tuning_save_and_load_roundtrip(tmp_path):
     path = tmp_path / "tune.txt"
     api.save_tuning(str(path))
     assert api.load_tuning(str(path)) >= 1
+
+
+def test_fma_peak_is_measured_and_fp32_outruns_fp64():
+    """The FMA-throughput probe gives positive rates below the nominal
+    per-SM ceilings (FP32: 128 FMA per clock per SM at the maximum clock)."""
+    stream = torch.cuda.current_stream().cuda_stream
+    f32 = C.sphericart_fma_peak(C.SPH_F32, stream, 2)
+    f64 = C.sphericart_fma_peak(C.SPH_F64, stream, 2)
+    props = torch.cuda.get_device_properties(0)
+    ceiling = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12  # TFLOP/s at 2.2 GHz
+    assert 0 < f64 < f32 < ceiling, (f32, f64, ceiling)
