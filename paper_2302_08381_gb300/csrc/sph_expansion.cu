@@ -3,11 +3,12 @@
 //   c[i, n, (l,m)] = sum_{k in centre i} R[k, n, l] * Y_l^m(x_k)
 //
 // for points (edge vectors) grouped by centre in CSR order. The harmonics are
-// never written to memory: one warp owns a centre, evaluates Y for 32 of its
-// points at a time (one lane per point, the unrolled recursion of the POINT
-// kernels, values only) into shared memory, stages the matching rows of R,
-// and then each lane accumulates the output columns it owns. Only the
-// coordinates, R and the [n_rad, K] result per centre touch HBM.
+// never written to memory: each warp owns a contiguous range of centres and
+// streams their points in 32-point chunks that cross centre boundaries; it
+// evaluates Y for a chunk (one lane per point, the unrolled recursion of the
+// POINT kernels, values only) into shared memory, stages the matching rows of
+// R, and then each lane accumulates the output columns it owns. Only the
+// coordinates, R, the offsets and the [n_rad, K] result per centre touch HBM.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -2,7 +2,9 @@
 
 Points are independent (arXiv 2302.08381, Section 3: the call is parallel over
 samples), so the path shards without any exchange: each rank evaluates its own
-points into its own outputs. Only the timing is reduced (max over ranks).
+points into its own outputs. Only the timing is reduced (max over ranks). The
+radial expansion (Eq. expansion) sums over the points of a centre; giving every
+rank whole centres keeps that sum on one GPU, so it needs no collective either.
 """
 
 from __future__ import annotations
@@ -17,6 +19,31 @@ def point_range(n_total: int, rank: int, world: int) -> tuple[int, int]:
     base, extra = divmod(n_total, world)
     start = rank * base + min(rank, extra)
     return start, start + base + (1 if rank < extra else 0)
+
+
+def centre_range(offsets, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous [first, end) slice of whole centres for `rank`, balanced by
+    points: rank r takes the centres whose first point lies in the r-th of
+    `world` equal point ranges (CSR `offsets`, non-decreasing, offsets[0] = 0).
+    A rank's point count differs from the even share by less than the largest
+    centre."""
+    import numpy as np
+
+    offsets = np.asarray(offsets, dtype=np.int64)
+    if offsets.ndim != 1 or offsets.size < 1 or offsets[0] != 0 or np.any(np.diff(offsets) < 0):
+        raise ValueError("offsets must be a non-decreasing CSR array starting at 0")
+    ncent = offsets.size - 1
+    n_total = int(offsets[-1])
+    starts = offsets[:-1]
+
+    def first_centre(r: int) -> int:
+        if r >= world:
+            return ncent
+        return int(np.searchsorted(starts, point_range(n_total, r, world)[0], side="left")) if r > 0 else 0
+
+    if world <= 0 or not (0 <= rank < world):
+        raise ValueError("bad partition arguments")
+    return first_centre(rank), first_centre(rank + 1)
 
 
 def set_bytes(n: int, l_max: int, gradients: bool = True, elem: int = 4) -> int:

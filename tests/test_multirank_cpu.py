@@ -34,6 +34,67 @@ def test_balance_sets_covers_and_balances():
         assert max(loads) - min(loads) <= biggest
 
 
+def test_centre_range_gives_whole_centres_balanced_by_points():
+    import numpy as np
+
+    rng = np.random.default_rng(7)
+    for counts in (rng.integers(0, 80, 5000), np.zeros(10, np.int64), np.array([1000, 1, 1, 1]), np.array([], np.int64)):
+        offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        n_total, big = int(offs[-1]), int(counts.max()) if counts.size else 0
+        for world in (1, 2, 3, 8):
+            ranges = [shard.centre_range(offs, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == counts.size
+            for (a, b), (c, d) in zip(ranges, ranges[1:]):
+                assert b == c and a <= b
+            for a, b in ranges:
+                assert abs(int(offs[b] - offs[a]) - n_total / world) <= big + 1
+    with pytest.raises(ValueError):
+        shard.centre_range(np.array([0, 5, 3]), 0, 2)
+
+
+def _expansion_worker(rank, world, port, q):
+    """Each rank expands its own whole centres (the oracle stands in for the
+    kernel); the concatenation over ranks must equal the expansion of all
+    centres, so no reduction of c is needed."""
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(8)
+        counts = rng.integers(0, 12, 41)
+        offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        xyz = inputs.shell_points(int(offs[-1]), 0.7, 3.0, seed=9).astype(np.float64)
+        R = inputs.upstream(int(offs[-1]), 2 * 4, seed=10).reshape(-1, 2, 4).astype(np.float64)
+        a, b = shard.centre_range(offs, rank, world)
+        mine = oracle.expansion(xyz[offs[a]:offs[b]], R[offs[a]:offs[b]], offs[a:b + 1] - offs[a], 3)
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        full = oracle.expansion(xyz, R, offs, 3)
+        q.put((rank, float(np.abs(np.concatenate(parts) - full).max()), [p.shape[0] for p in parts]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_gloo_expansion_by_whole_centres():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_expansion_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, err, sizes in res:
+        assert err == 0.0 and sum(sizes) == 41 and min(sizes) > 0
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
