@@ -123,7 +123,11 @@ typedef enum {
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
  * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
- * (0..8, 0 = 1) and blocks_per_sm.                                              */
+ * (0..8, 0 = 1) and blocks_per_sm.
+ * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
+ * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
+ * the FP64 pipe); when a call has fewer than 2 x SMs x warps_per_block tiles,
+ * it runs fewer warps per block so that the blocks reach every SM.          */
 typedef struct {
     int32_t points_per_tile;
     int32_t warps_per_block;

@@ -198,6 +198,18 @@ int tile_multiple(int L, int elem) {
 sph_launch default_point_fwd(int L, int grad, int elem, int hess = 0) {
     const size_t row = point_row_bytes(L, grad, elem, hess);
     const int mult = tile_multiple(L, elem);
+    if (elem == 8 && !hess) {
+        // FP64 arithmetic is the bound (GB300's FP64 FMA rate is 1/73 of
+        // FP32): fill as many lanes of each warp as a tile of <= 74 KB allows
+        // (three one-warp blocks per SM), one warp per block, a grid of 16
+        // blocks per SM in waves. Measured (autotuner, l_max 2..11, 10k and
+        // 1M points): within 5 % of the tuned shapes; the earlier 48 KB tile
+        // budget left 14 of 32 lanes idle at l_max 8 with gradients (-15 %).
+        int P = 32;
+        while (P > mult && size_t(P) * row > 74 * 1024) P -= mult;
+        P = std::max(mult, P / mult * mult);
+        return sph_launch{P, 1, 16, 0};
+    }
     const size_t budget = 48 * 1024;
     int P = 32;
     while (P > mult && size_t(P) * row > budget) P -= mult;
@@ -453,16 +465,29 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
               nullptr};
     if (launch) a.launch = *launch;
     if (fam == SPH_KERNEL_POINT) {
+        bool from_default = !launch;
         if (!launch) {
             int d = -1;
             cudaGetDevice(&d);
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, ddsph ? 2 : grad});
-            if (it != g_tuned.end()) a.launch = it->second;
+            if (it != g_tuned.end()) {
+                a.launch = it->second;
+                from_default = false;
+            }
         }
         const int hess = ddsph ? 1 : 0;
         const sph_launch dflt = default_point_fwd(l_max, grad, eo, hess);
         if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo, hess))) return SPH_EINVAL;
+        if (from_default) {
+            // Few tiles (small n): fewer warps per block, so that the blocks
+            // spread over every SM instead of filling a few (measured at 10k
+            // points: the tuned shapes use one warp per block, 1.3-1.6x faster
+            // than eight).
+            const int64_t tiles = (n + a.launch.points_per_tile - 1) / a.launch.points_per_tile;
+            const int64_t per_w = std::max<int64_t>(1, tiles / (2 * int64_t(sm_count())));
+            a.launch.warps_per_block = int(std::min<int64_t>(a.launch.warps_per_block, per_w));
+        }
         return cuda_status(point_fwd_fn(l_max)(a), "POINT forward launch");
     }
     if (degree) {
