@@ -265,7 +265,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "fwd64", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess"],
+        choices=["fwd", "fwd64", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess",
+                 "degree50_f64"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     args = ap.parse_args()
@@ -465,6 +466,8 @@ def run_profile(args):
         L = L_MAX
     elif args.profile in ("slice20", "degree20", "row20"):
         L = 20
+    elif args.profile == "degree50_f64":
+        L = 50
     else:
         L = BWD_L  # backward kernels and the expansion: l_max = 6
     K = (L + 1) ** 2
@@ -473,6 +476,9 @@ def run_profile(args):
         sph = torch.empty((n, K), device=dev)
         dsph = torch.empty((n, 3, K), device=dev)
         fn = lambda: api.spherical_harmonics(x, L, False, gradients=True, out=(sph, dsph))  # noqa: E731
+    elif args.profile == "degree50_f64":
+        x64d = x.double()
+        fn = lambda: api.spherical_harmonics(x64d, L, True, gradients=True)  # noqa: E731  (AUTO: DEGREE)
     elif args.profile == "fwd64":
         x64 = x.double()
         fn = lambda: api.spherical_harmonics(x64, L, False, gradients=True)  # noqa: E731
