@@ -82,6 +82,49 @@ class OraclePool:
         self.pool.join()
 
 
+def _oracle_subset(kind: str):
+    """One 10,000-point subset through the FP64 oracle in this process;
+    returns seconds."""
+    import numpy as np
+
+    import oracle
+    from paper_2302_08381_gb300 import inputs
+
+    if kind == "l8":  # the benchmark distribution, values + gradients
+        xyz = inputs.shell_points(10_000, 0.5, 5.0, seed=3).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.spherical_harmonics_grad(xyz, 8, False)
+    elif kind == "l50":  # half uniform on the sphere, half within 1e-4 rad of the poles, normalized
+        xyz = inputs.pole_mix_points(10_000, seed=4)
+        t0 = time.perf_counter()
+        oracle.spherical_harmonics_grad(xyz, 50, True)
+    else:  # ragged sets: 2,500 points at each l_max of {3, 6, 8, 12}
+        sets = [(inputs.normal_points(2_500, seed=10 + i), L) for i, L in enumerate((3, 6, 8, 12))]
+        t0 = time.perf_counter()
+        for xyz, L in sets:
+            oracle.spherical_harmonics_grad(xyz, L, False)
+    return time.perf_counter() - t0
+
+
+def time_oracle_single_thread():
+    """ns per point of the FP64 oracle on one host core (a spawned
+    one-process pool) for 10,000-point subsets: l_max 8 values + gradients
+    (the benchmark), l_max 50 normalized at the pole mix, and the ragged
+    l_max mix {3, 6, 8, 12}."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(1) as pool:
+        pool.map(_oracle_subset, ["batch"])  # import + warm the worker
+        secs = pool.map(_oracle_subset, ["l8", "l50", "batch"], chunksize=1)
+    return {
+        "cores": 1,
+        "l8_values_gradients_ns_per_point": secs[0] * 1e9 / 10_000,
+        "l50_normalized_pole_mix_ns_per_point": secs[1] * 1e9 / 10_000,
+        "ragged_lmax_3_6_8_12_ns_per_point": secs[2] * 1e9 / 10_000,
+        "sample": "10,000 points each, FP64 oracle, one spawned process",
+    }
+
+
 def time_oracle(total_points: int, l_max: int, chunk: int = 16384):
     """Times the FP64 oracle over total_points on all host cores.
     Returns (points/s, cores, seconds)."""
@@ -286,9 +329,11 @@ def main():
 
     # CPU baseline first: the spawn pool is created before any CUDA call.
     cpu = None
+    cpu_single = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.no_extras:
         sample = 1_048_576
         vps, cores, dt = time_oracle(sample, L_MAX)
+        cpu_single = time_oracle_single_thread()
         cpu = {
             "value": vps,
             "unit": "points/s",
@@ -444,6 +489,8 @@ def main():
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if cpu_single:
+            line["oracle_single_thread"] = cpu_single
         line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
