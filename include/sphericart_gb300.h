@@ -216,8 +216,12 @@ int sphericart_double_backward(const void* xyz, const void* g, const void* v,
  *   normalized 0: Y is the scaled r^l Y_l^m (the paper folds r^-l into R),
  *              1: Y_l^m on the unit sphere.  dtype: SPH_F32 or SPH_F64 for all.
  * l_max <= SPH_MAX_L_POINT, 1 <= n_rad <= 64. A centre whose offsets are not
- * non-decreasing within [0, n_points] gets zeros and sets bit 2 of the device
- * status word (sphericart_device_status); nothing outside the buffers is read. */
+ * non-decreasing within [0, n_points] gets zeros and ORs the value 2 into the
+ * device status word (sphericart_device_status); nothing outside the buffers
+ * is read. Returns SPH_EUNSUPPORTED when one warp's staging (32 harmonic
+ * rows, two buffers of 32 radial rows and a centre's sums) exceeds the
+ * device's shared memory (e.g. FP64 with l_max 16 and 64 radial channels).
+ * Each warp streams a contiguous range of centres in 32-point chunks. */
 int sphericart_expansion(const void* xyz, const void* radial, const int64_t* offsets,
                          int64_t n_centres, int64_t n_points, int n_rad, int l_max,
                          int normalized, int dtype, void* c, void* stream);
