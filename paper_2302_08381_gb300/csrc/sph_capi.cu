@@ -688,6 +688,8 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
             if (it != g_tuned.end()) s = it->second;
         }
         const sph_launch dflt = default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
+        // as resolve_point: no tuned shape at all takes the whole default
+        if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = dflt.blocks_per_sm;
         if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;
         if (s.warps_per_block == 0) s.warps_per_block = dflt.warps_per_block;
         *launch_out = s;

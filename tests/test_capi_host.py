@@ -265,3 +265,18 @@ def test_product_path_has_no_cpu_fallback():
 def test_fma_peak_argument_errors():
     assert _err(C.sphericart_fma_peak, 7, None, 3) == C.SPH_EINVAL
     assert _err(C.sphericart_fma_peak, C.SPH_F32, None, 0) == C.SPH_EINVAL
+
+
+def test_point_default_shapes():
+    """The POINT default (no shape given, none tuned): FP32 fills ~48 KB
+    tiles with several warps per block; FP64, bound by the FP64 pipe, fills
+    up to 32 points within 74 KB with one warp per block."""
+    fam, s = C.sphericart_launch_info(8, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_POINT and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (32, 4, 16)
+    fam, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_POINT and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (28, 1, 16)
+    assert 28 * 4 * 81 * 8 <= 74 * 1024 < 30 * 4 * 81 * 8  # the largest even tile inside 74 KB
+    _, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)
+    assert (s.points_per_tile, s.warps_per_block) == (32, 1)
+    _, s = C.sphericart_launch_info(11, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
+    assert (s.points_per_tile, s.warps_per_block) == (16, 1)
