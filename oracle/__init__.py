@@ -12,9 +12,11 @@ from .sph_oracle import (  # noqa: F401
     prefactor,
     prefactor_table,
     legendre_table,
+    legendre_derivative_table,
     spherical_harmonics,
     spherical_harmonics_grad,
     spherical_harmonics_hessian,
+    spherical_harmonics_hessian_fd,
     backward,
     double_backward,
     column,

@@ -13,9 +13,13 @@ What it computes (arXiv 2302.08381, Section 2):
 * the scaled (solid) form ``r^l Y_l^m`` of Section 2 and the "normalized" form
   ``Y_l^m`` on the unit sphere of Section 3.
 * Cartesian gradients by the analytic chain rule in spherical coordinates.
-* Hessians by central differences of the analytic gradient with Richardson
-  extrapolation (the paper gives no Hessian formulas; it only claims derivatives
-  of any order follow from Eq. iter-deri).
+* Hessians by the analytic second derivative of the same spherical-coordinate
+  definition (the paper gives no Hessian formulas; it only claims derivatives
+  of any order follow from Eq. iter-deri). The theta dependence is written with
+  the t-derivatives of the Legendre polynomials, P_l^m = (-1)^m sin^m(theta)
+  d^m P_l/dt^m, so every power of sin(theta) is explicit and no term divides by
+  it; a finite-difference Hessian (Richardson-extrapolated central differences
+  of the analytic gradient) is kept as a cross-check.
 * the adjoints used by autograd: ``dL/dxyz = sum_k g_k dY_k/dxyz`` and the double
   backward built on the Hessian.
 * the radial expansion of Eq. expansion, ``c_{nlm} = sum_k R_{nl}(r_k) Y_l^m(r_k)``
@@ -41,9 +45,12 @@ Readings of the paper taken here (the paper is silent or ambiguous):
 Pins (tests/test_oracle_pins.py): textbook closed forms for l <= 3, a library
 routine (scipy's complex spherical harmonics), the addition theorem, exact
 quadrature orthonormality, rotation invariance, central finite differences for
-gradients, the gradient block-norm identity, and for the Hessian its symmetry,
-the harmonic (Laplace) property and Euler's homogeneity relation. Every
-function below is pinned; none is "parity unpinned".
+gradients, the gradient block-norm identity, and for the Hessian the closed
+forms, the finite-difference Hessian, the addition theorem differentiated twice
+(with numpy's Legendre series), the exact Hessian block norm
+sum_m |d_i d_j r^l Y_l^m|^2 = r^(2l-4) l (l-1) (2l-1) (2l+1)^2 / (4 pi), its
+symmetry, the harmonic (Laplace) property and Euler's homogeneity relation.
+Every function below is pinned; none is "parity unpinned".
 """
 
 from __future__ import annotations
@@ -59,9 +66,11 @@ __all__ = [
     "prefactor",
     "prefactor_table",
     "legendre_table",
+    "legendre_derivative_table",
     "spherical_harmonics",
     "spherical_harmonics_grad",
     "spherical_harmonics_hessian",
+    "spherical_harmonics_hessian_fd",
     "backward",
     "double_backward",
     "expansion",
@@ -240,13 +249,126 @@ def spherical_harmonics_grad(xyz, l_max: int, normalized: bool = False):
     return vals, grad
 
 
-def spherical_harmonics_hessian(xyz, l_max: int, normalized: bool = False, h=None):
-    """Hessians [n, 3, 3, K] by differences of the analytic gradient.
+def legendre_derivative_table(l_max: int, t: np.ndarray, extra: int = 2) -> np.ndarray:
+    """t-derivatives of the Legendre polynomials: ``A[l, m]`` = d^m P_l / dt^m.
+
+    Shape [l_max+1, l_max+1+extra, ...t.shape]; entries with m > l are 0 (P_l
+    has degree l). With the Condon-Shortley sign of Eq. recur-p,
+    P_l^m(t) = (-1)^m (1-t^2)^(m/2) A[l, m], so A obeys the recursion of Eq.
+    recur-p with the common factor (-1)^m sin^m(theta) divided out:
+    A_m^m = (2m-1)!!, A_{m+1}^m = (2m+1) t A_m^m and
+    (l-m) A_l^m = (2l-1) t A_{l-1}^m - (l+m-1) A_{l-2}^m.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    A = np.zeros((l_max + 1, l_max + 1 + extra) + t.shape)
+    seed = 1.0  # (2m-1)!!, starting from (-1)!! = 1
+    for m in range(0, l_max + 1):
+        if m > 0:
+            seed *= 2 * m - 1
+        A[m, m] = seed
+        if m + 1 <= l_max:
+            A[m + 1, m] = (2 * m + 1) * t * seed
+        for l in range(m + 2, l_max + 1):
+            A[l, m] = ((2 * l - 1) * t * A[l - 1, m] - (l + m - 1) * A[l - 2, m]) / (l - m)
+    return A
+
+
+def _sin_power(u: np.ndarray, k: int) -> np.ndarray:
+    """sin(theta)^k for k >= 0; 0 for k < 0, where every caller's coefficient is 0."""
+    if k < 0:
+        return np.zeros_like(u)
+    return u ** k
+
+
+def spherical_harmonics_hessian(xyz, l_max: int, normalized: bool = False) -> np.ndarray:
+    """Hessians [n, 3, 3, K] in FP64, analytic; H[:, i, j, k] = d^2 Y_k / dx_i dx_j.
+
+    With f = r^p Y(theta, phi) (p = l for the scaled form, p = 0 for the
+    normalized one), the gradient is G = r^(p-1) v with
+    v = p Y r_hat + Y_theta theta_hat + W phi_hat and W = Y_phi / sin(theta).
+    Differentiating G once more in spherical coordinates (d r_hat/d theta =
+    theta_hat, d theta_hat/d theta = -r_hat, d r_hat/d phi = sin(theta) phi_hat,
+    d theta_hat/d phi = cos(theta) phi_hat, d phi_hat/d phi =
+    -(sin(theta) r_hat + cos(theta) theta_hat)) gives
+
+        H_ij = r^(p-2) [ (p-1) v_i r_hat_j + a_i theta_hat_j + b_i phi_hat_j ],
+        a = (p-1) Y_theta r_hat + (p Y + Y_theta_theta) theta_hat + W_theta phi_hat,
+        b = (p-1) W r_hat + W_theta theta_hat + (p Y + Z) phi_hat,
+
+    with Z = cot(theta) Y_theta + Y_phi_phi / sin^2(theta). For one (l, m),
+    Y = F_l^|m| P_l^|m|(cos theta) T(phi) (Eq. real-sh-spherical). Writing
+    P = (-1)^m s^m A0 with s = sin(theta), t = cos(theta) and A0, A1, A2 the
+    m-th, (m+1)-th and (m+2)-th t-derivatives of P_l (dt/dtheta = -s):
+
+        P_theta       = (-1)^m [m s^(m-1) t A0 - s^(m+1) A1]
+        P_theta_theta = (-1)^m [m(m-1) s^(m-2) t^2 A0 - m s^m A0
+                                - (2m+1) s^m t A1 + s^(m+2) A2]
+        d(P/s)/dtheta = (-1)^m [(m-1) s^(m-2) t A0 - s^m A1]
+        cot P_theta - m^2 P/s^2 = (-1)^m [m(1-m) s^(m-2) A0 - m s^m A0 - t s^m A1]
+
+    (the last uses t^2 = 1 - s^2). Every negative power of s carries a
+    coefficient that vanishes for the m where it would be negative, so the
+    expressions are finite on the z axis. At r = 0 the scaled Hessian is the
+    polynomial's (constant for l = 2, zero otherwise); the normalized one is 0.
+    """
+    r, t, u, phi = _angles(xyz)
+    n = r.shape[0]
+    K = (l_max + 1) ** 2
+    H = np.zeros((n, 3, 3, K))
+    A = legendre_derivative_table(l_max, t)
+    cp, sp_ = np.cos(phi), np.sin(phi)
+    zero = np.zeros_like(cp)
+    rhat = np.stack([u * cp, u * sp_, t], axis=1)  # [n, 3]
+    that = np.stack([t * cp, t * sp_, -u], axis=1)
+    phat = np.stack([-sp_, cp, zero], axis=1)
+    at_origin = r == 0
+    rsafe = np.where(at_origin, 1.0, r)
+    inv_sqrt2 = 1.0 / math.sqrt(2.0)
+    for l in range(l_max + 1):
+        p = 0.0 if normalized else float(l)
+        # r^(p-2); the origin is filled in below.
+        rp2 = rsafe ** (p - 2.0)
+        for m in range(-l, l + 1):
+            am = abs(m)
+            cF = prefactor(l, am) * (-1.0 if am % 2 else 1.0)
+            A0, A1, A2 = A[l, am], A[l, am + 1], A[l, am + 2]
+            s_m2, s_m1 = _sin_power(u, am - 2), _sin_power(u, am - 1)
+            s_m, s_p1, s_p2 = _sin_power(u, am), _sin_power(u, am + 1), _sin_power(u, am + 2)
+            P0 = cF * s_m * A0
+            Pt = cF * (am * s_m1 * t * A0 - s_p1 * A1)
+            Ptt = cF * (am * (am - 1) * s_m2 * t * t * A0 - am * s_m * A0
+                        - (2 * am + 1) * s_m * t * A1 + s_p2 * A2)
+            Pbt = cF * ((am - 1) * s_m2 * t * A0 - s_m * A1)
+            Pz = cF * (am * (1 - am) * s_m2 * A0 - am * s_m * A0 - t * s_m * A1)
+            Pb = cF * s_m1 * A0
+            if m < 0:
+                T, dT = np.sin(am * phi), am * np.cos(am * phi)
+            elif m == 0:
+                T, dT = np.full_like(phi, inv_sqrt2), zero
+            else:
+                T, dT = np.cos(m * phi), -m * np.sin(m * phi)
+            Yv, Yt, Ytt, Z = P0 * T, Pt * T, Ptt * T, Pz * T
+            W, Wt = Pb * dT, Pbt * dT
+            v = p * Yv[:, None] * rhat + Yt[:, None] * that + W[:, None] * phat
+            a = (p - 1.0) * Yt[:, None] * rhat + (p * Yv + Ytt)[:, None] * that + Wt[:, None] * phat
+            b = (p - 1.0) * W[:, None] * rhat + Wt[:, None] * that + (p * Yv + Z)[:, None] * phat
+            Hk = ((p - 1.0) * v[:, :, None] * rhat[:, None, :] + a[:, :, None] * that[:, None, :]
+                  + b[:, :, None] * phat[:, None, :])
+            Hk = Hk * rp2[:, None, None]
+            if normalized or l != 2:
+                Hk[at_origin] = 0.0
+            H[:, :, :, column(l, m)] = Hk
+    return H
+
+
+def spherical_harmonics_hessian_fd(xyz, l_max: int, normalized: bool = False, h=None):
+    """Hessians [n, 3, 3, K] by differences of the analytic gradient (cross-check).
 
     Central differences with step h and h/2 combined by one Richardson step
     (error O(h^4)); h defaults to 1e-3 * max(r, 1e-3). H[:, i, j, k] is
     d^2 Y_k / dx_i dx_j. Used at l_max <= 16, where the truncation error is
-    below ~1e-8 relative to the Hessian's block scale.
+    below ~1e-8 relative to the Hessian's block scale. It shares only the
+    gradient with ``spherical_harmonics_hessian`` and pins it.
     """
     xyz = np.asarray(xyz, dtype=np.float64)
     n = xyz.shape[0]

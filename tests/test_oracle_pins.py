@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 import scipy.special as sps
 import sympy as sp
+from numpy.polynomial import legendre as npl
 
 import oracle.sph_oracle as orc
 from oracle import (
@@ -25,6 +26,7 @@ from oracle import (
     spherical_harmonics,
     spherical_harmonics_grad,
     spherical_harmonics_hessian,
+    spherical_harmonics_hessian_fd,
 )
 from paper_2302_08381_gb300 import inputs
 
@@ -296,17 +298,55 @@ def test_gradient_finite_differences(normalized, kind):
     del r
 
 
-def test_gradient_block_norm_identity():
-    """sum_m |grad (r^l Y_l^m)|^2 = r^(2l-2) l (2l+1)^2 / (4 pi)."""
-    l_max = 30
-    xyz = inputs.shell_points(80, 0.5, 1.5, seed=22, dtype=np.float64)
+@pytest.mark.parametrize("kind", ["shell", "pole"])
+def test_gradient_block_norm_identity(kind):
+    """sum_m |grad (r^l Y_l^m)|^2 = r^(2l-2) l (2l+1)^2 / (4 pi), every l up to 50,
+    on shell points and on points 1e-9..1e-4 rad from both poles."""
+    l_max = 50
+    if kind == "shell":
+        xyz = inputs.shell_points(80, 0.5, 1.5, seed=22, dtype=np.float64)
+    else:
+        xyz = inputs.pole_mix_points(80, seed=122) * 1.2
     _, g = spherical_harmonics_grad(xyz, l_max)
     r = np.linalg.norm(xyz, axis=1)
     for l in range(1, l_max + 1):
         s = slice(l * l, (l + 1) ** 2)
         lhs = np.sum(g[:, :, s] ** 2, axis=(1, 2))
         rhs = r ** (2 * l - 2) * l * (2 * l + 1) ** 2 / (4 * math.pi)
-        np.testing.assert_allclose(lhs, rhs, rtol=1e-11)
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_gradient_addition_theorem(normalized):
+    """Addition theorem differentiated once in x, every l up to 50, pole mix:
+    sum_m grad Y_l^m(x) Y_l^m(y) = (2l+1)/(4 pi) grad_x [|x|^p |y|^l P_l(x_hat . y_hat)]
+    = (2l+1)/(4 pi) |y|^l r^(p-1) [p P x_hat + P' (y_hat - s x_hat)]."""
+    l_max, n = 50, 40
+    x = np.concatenate([inputs.pole_mix_points(n, seed=160) * 1.4,
+                        inputs.shell_points(n, 0.5, 1.5, seed=161, dtype=np.float64)])
+    _, G = spherical_harmonics_grad(x, l_max, normalized)
+    r = np.linalg.norm(x, axis=1)
+    xh = x / r[:, None]
+    worst = 0.0
+    for trial in range(3):
+        yv = inputs.shell_points(2 * n, 0.5, 1.5, seed=162 + trial, dtype=np.float64)
+        Ry = spherical_harmonics(yv, l_max, normalized)
+        ry = np.linalg.norm(yv, axis=1)
+        yh = yv / ry[:, None]
+        s_ = np.sum(xh * yh, axis=1)
+        for l in range(l_max + 1):
+            sl = slice(l * l, (l + 1) ** 2)
+            lhs = np.einsum("nik,nk->ni", G[:, :, sl], Ry[:, sl])
+            e = np.zeros(l + 1)
+            e[l] = 1.0
+            P = npl.legval(s_, e)
+            P1 = npl.legval(s_, npl.legder(e)) if l >= 1 else 0.0 * s_
+            p = 0.0 if normalized else float(l)
+            c = (2 * l + 1) / (4 * math.pi) * (np.ones(2 * n) if normalized else ry**l)
+            rhs = (c * r ** (p - 1))[:, None] * ((p * P)[:, None] * xh + P1[:, None] * (yh - s_[:, None] * xh))
+            scale = c * r ** (p - 1) * (l + 1)
+            worst = max(worst, float(np.max(np.abs(lhs - rhs) / scale[:, None])))
+    assert worst < 1e-13, worst
 
 
 def test_gradient_euler_homogeneity():
@@ -321,28 +361,189 @@ def test_gradient_euler_homogeneity():
 
 
 # --------------------------------------------------------------------------- Hessians
-def test_hessian_closed_forms():
-    xyz = inputs.normal_points(40, seed=24)
-    _, _, H = _closed_eval(xyz)
-    got = spherical_harmonics_hessian(xyz, 3)
-    np.testing.assert_allclose(got, H, atol=1e-9)
+def _hess_block_scale(l_max, r, normalized=False):
+    """[n, K]: exact rms size of an l block's Hessian (scaled form), also used
+    as the error scale of the normalized one with r^(l-2) -> r^-2."""
+    lv = np.concatenate([np.full(2 * l + 1, l) for l in range(l_max + 1)]).astype(np.float64)
+    c = np.sqrt(np.maximum(lv * (lv - 1) * (2 * lv - 1), 1.0) * (2 * lv + 1) ** 2 / (4 * math.pi))
+    pw = np.full_like(lv, -2.0) if normalized else np.maximum(lv - 2, 0)
+    return c[None, :] * r[:, None] ** pw[None, :]
 
 
-@pytest.mark.parametrize("l_max", [6, 12])
-def test_hessian_harmonic_and_euler(l_max):
-    """trace H = 0 (solid harmonics are harmonic); sum_j x_j H_ij = (l-1) d_i Y."""
-    xyz = inputs.shell_points(40, 0.7, 2.0, seed=25, dtype=np.float64)
+def _closed_eval_normalized(xyz):
+    """Hessians of r^-l times the closed forms (the normalized harmonics), via sympy."""
+    n = xyz.shape[0]
+    H = np.zeros((n, 3, 3, 16))
+    syms = (X, Y_, Z)
+    args = (xyz[:, 0], xyz[:, 1], xyz[:, 2])
+    rr = sp.sqrt(X**2 + Y_**2 + Z**2)
+    for (l, m), e in CLOSED.items():
+        k = column(l, m)
+        f = e / rr**l
+        for i in range(3):
+            for j in range(i, 3):
+                val = np.broadcast_to(_lambd(sp.diff(f, syms[i], syms[j]))(*args), (n,))
+                H[:, i, j, k] = val
+                H[:, j, i, k] = val
+    return H
+
+
+def _hessian_pin_points():
+    """General points, points 1e-9..1e-4 rad from both poles, and exact z-axis points."""
+    gen = inputs.normal_points(40, seed=24)
+    pole = inputs.pole_mix_points(40, seed=124) * 1.7
+    axis = np.array([[0.0, 0.0, 1.3], [0.0, 0.0, -0.6], [1e-12, 0.0, 2.0]])
+    return np.concatenate([gen, pole, axis])
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_hessian_closed_forms(normalized):
+    """Analytic Hessian vs sympy's second derivatives of the l <= 3 closed forms."""
+    xyz = _hessian_pin_points()
+    if normalized:
+        ref = _closed_eval_normalized(xyz)
+    else:
+        _, _, ref = _closed_eval(xyz)
+    got = spherical_harmonics_hessian(xyz, 3, normalized)
+    scale = _hess_block_scale(3, np.linalg.norm(xyz, axis=1), normalized)[:, None, None, :]
+    assert np.max(np.abs(got - ref) / scale) < 1e-13
+
+
+def _legendre_kernel_hessian(x, yv, l, p):
+    """d_i d_j of r^p P_l(x_hat . y_hat) in x, with numpy's Legendre series.
+
+    With s = x_hat . y_hat and b = y_hat - s x_hat, direct differentiation
+    gives r^(p-2) [p(p-1) P x_hat x_hat^T + (p-1) P' (x_hat b^T + b x_hat^T)
+    + (p P - s P') (I - x_hat x_hat^T) + P'' b b^T].
+    """
+    r = np.linalg.norm(x, axis=1)
+    xh = x / r[:, None]
+    a = yv / np.linalg.norm(yv, axis=1)[:, None]
+    s = np.sum(xh * a, axis=1)
+    e = np.zeros(l + 1)
+    e[l] = 1.0
+    P = npl.legval(s, e)
+    P1 = npl.legval(s, npl.legder(e)) if l >= 1 else 0.0 * s
+    P2 = npl.legval(s, npl.legder(e, 2)) if l >= 2 else 0.0 * s
+    b = a - s[:, None] * xh
+    outer = lambda u, w: u[:, :, None] * w[:, None, :]  # noqa: E731
+    H = ((p * (p - 1) * P)[:, None, None] * outer(xh, xh)
+         + ((p - 1) * P1)[:, None, None] * (outer(xh, b) + outer(b, xh))
+         + (p * P - s * P1)[:, None, None] * (np.eye(3)[None] - outer(xh, xh))
+         + P2[:, None, None] * outer(b, b))
+    return H * (r ** (p - 2.0))[:, None, None]
+
+
+def test_legendre_kernel_hessian_formula():
+    """The test's own kernel formula against sympy (so the pin below stands on it)."""
+    x = inputs.shell_points(5, 0.5, 1.5, seed=140, dtype=np.float64)
+    yv = inputs.shell_points(5, 0.5, 1.5, seed=141, dtype=np.float64)
+    a1, a2, a3 = sp.symbols("a1 a2 a3", real=True)
+    for l, p in ((3, 3), (4, 0), (5, 5)):
+        rr = sp.sqrt(X**2 + Y_**2 + Z**2)
+        s_ = (X * a1 + Y_ * a2 + Z * a3) / rr
+        f = rr**p * sp.legendre(l, s_)
+        got = _legendre_kernel_hessian(x, yv, l, p)
+        yh = yv / np.linalg.norm(yv, axis=1)[:, None]
+        for i, si in enumerate((X, Y_, Z)):
+            for j, sj in enumerate((X, Y_, Z)):
+                fn = sp.lambdify((X, Y_, Z, a1, a2, a3), sp.diff(f, si, sj), "numpy")
+                ref = fn(x[:, 0], x[:, 1], x[:, 2], yh[:, 0], yh[:, 1], yh[:, 2])
+                np.testing.assert_allclose(got[:, i, j], ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+@pytest.mark.parametrize("kind", ["shell", "pole"])
+def test_hessian_addition_theorem(normalized, kind):
+    """Addition theorem differentiated twice in x, every l up to 50:
+
+    sum_m d_i d_j Y_l^m(x) Y_l^m(y) = (2l+1)/(4 pi) d_i d_j [|x|^p |y|^l P_l(x_hat . y_hat)]
+
+    (p = l scaled, p = 0 and |y|^0 normalized). Three generic y per x fix
+    every m component of each block."""
+    l_max, n = 50, 40
+    if kind == "shell":
+        x = inputs.shell_points(n, 0.5, 1.5, seed=142, dtype=np.float64)
+    else:
+        x = inputs.pole_mix_points(n, seed=143) * 1.3
+    H = spherical_harmonics_hessian(x, l_max, normalized)
+    r = np.linalg.norm(x, axis=1)
+    worst = 0.0
+    for trial in range(3):
+        yv = inputs.shell_points(n, 0.5, 1.5, seed=144 + trial, dtype=np.float64)
+        Ry = spherical_harmonics(yv, l_max, normalized)
+        ry = np.linalg.norm(yv, axis=1)
+        for l in range(l_max + 1):
+            sl = slice(l * l, (l + 1) ** 2)
+            lhs = np.einsum("nijk,nk->nij", H[..., sl], Ry[:, sl])
+            c = (2 * l + 1) / (4 * math.pi) * (np.ones(n) if normalized else ry**l)
+            rhs = _legendre_kernel_hessian(x, yv, l, 0 if normalized else l) * c[:, None, None]
+            scale = c * (r ** (-2.0) if normalized else r ** (l - 2.0)) * (l + 1) ** 2
+            worst = max(worst, float(np.max(np.abs(lhs - rhs) / scale[:, None, None])))
+    assert worst < 1e-13, worst
+
+
+@pytest.mark.parametrize("kind", ["shell", "pole"])
+def test_hessian_block_norm_identity(kind):
+    """sum_m |d_i d_j (r^l Y_l^m)|^2 = r^(2l-4) l (l-1) (2l-1) (2l+1)^2 / (4 pi),
+    every l up to 50 (the constant follows from the addition theorem; it is
+    rotation invariant and was evaluated exactly at the pole)."""
+    l_max = 50
+    if kind == "shell":
+        x = inputs.shell_points(60, 0.5, 1.5, seed=150, dtype=np.float64)
+    else:
+        x = inputs.pole_mix_points(60, seed=151) * 0.8
+    H = spherical_harmonics_hessian(x, l_max)
+    r = np.linalg.norm(x, axis=1)
+    for l in range(l_max + 1):
+        sl = slice(l * l, (l + 1) ** 2)
+        lhs = np.sum(H[..., sl] ** 2, axis=(1, 2, 3))
+        rhs = r ** (2 * l - 4.0) * l * (l - 1) * (2 * l - 1) * (2 * l + 1) ** 2 / (4 * math.pi)
+        if l < 2:
+            assert np.max(np.abs(lhs)) < 1e-26
+        else:
+            np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+@pytest.mark.parametrize("l_max", [6, 20])
+def test_hessian_harmonic_euler_symmetric(l_max):
+    """trace H = 0 (solid harmonics are harmonic); sum_j x_j H_ij = (l-1) d_i Y;
+    H symmetric; all to FP64 rounding."""
+    xyz = np.concatenate([inputs.shell_points(40, 0.7, 2.0, seed=25, dtype=np.float64),
+                          inputs.pole_mix_points(20, seed=125)])
     _, g = spherical_harmonics_grad(xyz, l_max)
     H = spherical_harmonics_hessian(xyz, l_max)
-    r = np.linalg.norm(xyz, axis=1)
-    lv = np.concatenate([np.full(2 * l + 1, l) for l in range(l_max + 1)])
-    hs = r[:, None] ** np.maximum(lv - 2, 0)[None, :] * (lv[None, :] + 1.0) ** 2.5
+    hs = _hess_block_scale(l_max, np.linalg.norm(xyz, axis=1))
     tr = np.trace(H, axis1=1, axis2=2)
-    assert np.max(np.abs(tr) / hs) < 1e-8
+    assert np.max(np.abs(tr) / hs) < 1e-13
     lhs = np.einsum("nj,nijk->nik", xyz, H)
+    lv = np.concatenate([np.full(2 * l + 1, l) for l in range(l_max + 1)])
     rhs = (lv[None, None, :] - 1.0) * g
-    assert np.max(np.abs(lhs - rhs) / hs[:, None, :]) < 1e-8
-    assert np.array_equal(H, H.transpose(0, 2, 1, 3))
+    assert np.max(np.abs(lhs - rhs) / hs[:, None, :]) < 1e-13
+    assert np.max(np.abs(H - H.transpose(0, 2, 1, 3)) / hs[:, None, None, :]) < 1e-13
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_hessian_matches_finite_differences(normalized):
+    """Analytic Hessian vs Richardson central differences of the analytic gradient."""
+    l_max = 12
+    xyz = np.concatenate([inputs.shell_points(30, 0.7, 2.0, seed=152, dtype=np.float64),
+                          inputs.near_pole_points(10, 1e-3, seed=153)])
+    H = spherical_harmonics_hessian(xyz, l_max, normalized)
+    Hfd = spherical_harmonics_hessian_fd(xyz, l_max, normalized)
+    hs = _hess_block_scale(l_max, np.linalg.norm(xyz, axis=1), normalized)
+    assert np.max(np.abs(H - Hfd) / hs[:, None, None, :]) < 1e-8
+
+
+def test_hessian_at_origin():
+    """r = 0: scaled Hessians are the constant ones of the l = 2 polynomials
+    (zero otherwise); normalized ones are 0 by convention."""
+    o = np.zeros((1, 3))
+    _, _, ref = _closed_eval(o)
+    H = spherical_harmonics_hessian(o, 4)
+    np.testing.assert_allclose(H[..., :16], ref, atol=1e-15)
+    assert np.all(H[..., 16:] == 0)
+    assert np.all(spherical_harmonics_hessian(o, 4, True) == 0)
 
 
 # --------------------------------------------------------------------------- adjoints
@@ -443,6 +644,66 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not pins_pass()
     monkeypatch.undo()
     assert pins_pass()
+
+
+def _patched(func, old, new):
+    """A copy of an oracle function with one source fragment replaced (a planted slip)."""
+    import inspect
+    import textwrap
+
+    src = textwrap.dedent(inspect.getsource(func))
+    assert src.count(old) == 1, old
+    ns = dict(func.__globals__)
+    exec(compile(src.replace(old, new), "<planted>", "exec"), ns)
+    return ns[func.__name__]
+
+
+@pytest.mark.parametrize(
+    "old,new",
+    [
+        # drop the -m s^m A0 term of P_theta_theta
+        ("- am * s_m * A0\n                        - (2 * am + 1)", "\n                        - (2 * am + 1)"),
+        # (2m+1) -> (2m) in P_theta_theta
+        ("(2 * am + 1) * s_m * t * A1", "(2 * am) * s_m * t * A1"),
+        # sign slip in d(P/s)/dtheta
+        ("Pbt = cF * ((am - 1) * s_m2 * t * A0 - s_m * A1)", "Pbt = cF * ((am - 1) * s_m2 * t * A0 + s_m * A1)"),
+        # theta_hat / phi_hat swapped in the phi-derivative row
+        ("+ Wt[:, None] * that + (p * Yv + Z)[:, None] * phat", "+ Wt[:, None] * phat + (p * Yv + Z)[:, None] * that"),
+        # (p-1) -> p in the radial term
+        ("Hk = ((p - 1.0) * v[:, :, None]", "Hk = (p * v[:, :, None]"),
+        # one wrong coefficient in the t-derivative recursion's seed
+        ("A[m + 1, m] = (2 * m + 1) * t * seed", "A[m + 1, m] = (2 * m + 2) * t * seed"),
+    ],
+)
+def test_planted_hessian_mistakes_are_caught(old, new, monkeypatch):
+    """Each slip planted in the analytic Hessian (on the CPU) fails a pin: the
+    closed forms (l <= 3), or the twice-differentiated addition theorem (l <= 8)."""
+    xyz = _hessian_pin_points()
+    _, _, ref = _closed_eval(xyz)
+    if "A[m + 1, m]" in old:
+        monkeypatch.setattr(orc, "legendre_derivative_table", _patched(orc.legendre_derivative_table, old, new))
+        hess = orc.spherical_harmonics_hessian
+    else:
+        hess = _patched(orc.spherical_harmonics_hessian, old, new)
+    got = hess(xyz, 3)
+    scale = _hess_block_scale(3, np.linalg.norm(xyz, axis=1))[:, None, None, :]
+    closed_ok = np.max(np.abs(got - ref) / scale) < 1e-13
+    x = inputs.shell_points(20, 0.5, 1.5, seed=170, dtype=np.float64)
+    yv = inputs.shell_points(20, 0.5, 1.5, seed=171, dtype=np.float64)
+    H = hess(x, 8)
+    Ry = spherical_harmonics(yv, 8)
+    ry = np.linalg.norm(yv, axis=1)
+    add_ok = True
+    for l in range(9):
+        sl = slice(l * l, (l + 1) ** 2)
+        lhs = np.einsum("nijk,nk->nij", H[..., sl], Ry[:, sl])
+        rhs = _legendre_kernel_hessian(x, yv, l, l) * ((2 * l + 1) / (4 * math.pi) * ry**l)[:, None, None]
+        add_ok &= bool(np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12))
+    assert not (closed_ok and add_ok)
+    # the unmodified oracle passes both
+    monkeypatch.undo()
+    got = orc.spherical_harmonics_hessian(xyz, 3)
+    assert np.max(np.abs(got - ref) / scale) < 1e-13
 
 
 # --------------------------------------------------------------- expansion
