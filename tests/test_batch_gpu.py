@@ -1,13 +1,15 @@
 """Ragged persistent batch: every set equals its own single-set launch
-(bitwise at equal tile sizes, else within FP32 rounding) and the oracle."""
+(within FP32 rounding) and, at every point, the oracle; the 512-set serving
+workload is checked at every point too."""
 
 import numpy as np
 import pytest
 import torch
 
+import full_parity
 import oracle
 from paper_2302_08381_gb300 import api, inputs
-from parity_utils import F32_GRAD, F32_VAL, assert_grads, assert_values, grad_scale, value_scale
+from parity_utils import F32_GRAD, F32_VAL, assert_grads, assert_values, grad_scale, value_bound, value_scale
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -38,9 +40,8 @@ def test_batch_matches_single_launch_and_oracle(normalized, mode):
             dg = (plan.dsph[i] - g).abs().double().cpu().numpy() / grad_scale(p, L, normalized)[:, None, :]
             assert dv.max() < 5e-6 and dg.max() < 5e-6, (i, L, dv.max(), dg.max())
         if p.shape[0]:
-            k = min(200, p.shape[0])
-            assert_values(plan.sph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_VAL)
-            assert_grads(plan.dsph[i][:k].double().cpu().numpy(), p[:k], L, normalized, F32_GRAD)
+            assert_values(plan.sph[i].double().cpu().numpy(), p, L, normalized, F32_VAL)
+            assert_grads(plan.dsph[i].double().cpu().numpy(), p, L, normalized, F32_GRAD)
     n, t = plan.info()
     assert n == sum(x.shape[0] for x in xs) and t > 0
     plan.close()
@@ -102,3 +103,26 @@ def test_batch_modes_agree():
         assert dv.max() < 5e-6 and dg.max() < 5e-6, (i, L, dv.max(), dg.max())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mode", ["per_lmax", "one_launch"])
+def test_batch_serving_workload_full(mode):
+    """512 sets, sizes log-uniform in [1,000, 200,000], l_max from {3, 6, 8, 12},
+    N(0,1) FP32 points (seed 5), values + gradients in the batch launch the
+    benchmark times: every point of every set against the oracle, one l_max
+    class at a time."""
+    xs, ls, xyz, offs = _sets(512, [3, 6, 8, 12], 1000, 200000, seed=5)
+    plan = api.BatchPlan(xs, ls, mode=mode)
+    plan.execute()
+    torch.cuda.synchronize()
+    for L in sorted(set(ls)):
+        ids = [i for i, v in enumerate(ls) if v == L]
+        p = np.concatenate([xyz[offs[i]:offs[i + 1]] for i in ids]).astype(np.float64)
+        s = torch.cat([plan.sph[i] for i in ids]).cpu().numpy()
+        d = torch.cat([plan.dsph[i] for i in ids]).cpu().numpy()
+        ev, eg, finite = full_parity.forward_errors(p, L, False, s, d)
+        assert finite
+        assert np.all(ev <= value_bound(L, F32_VAL)), (L, ev)
+        assert np.all(eg <= F32_GRAD), (L, eg)
+        del s, d
+    plan.close()

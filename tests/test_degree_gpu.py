@@ -80,7 +80,7 @@ def test_f64_values_and_gradients(kernel, normalized):
         v, g = _run(xyz, l_max, normalized, True, kernel, dtype=torch.float64)
         rv, rg = oracle.spherical_harmonics_grad(xyz, l_max, normalized)
         assert_values(v, xyz, l_max, normalized, F64_TOL, ref=rv)
-        assert_grads(g, xyz, l_max, normalized, F64_TOL * 10, ref=rg)
+        assert_grads(g, xyz, l_max, normalized, F64_TOL, ref=rg)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -119,7 +119,7 @@ def test_pole_mix_f64(kernel, l_max):
     rv, rg = oracle.spherical_harmonics_grad(xyz, l_max, True)
     v, g = _run(xyz, l_max, True, True, kernel, dtype=torch.float64)
     assert_values(v, xyz, l_max, True, F64_TOL, ref=rv)
-    assert_grads(g, xyz, l_max, True, 1e-11, ref=rg)
+    assert_grads(g, xyz, l_max, True, F64_TOL, ref=rg)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -142,7 +142,7 @@ def test_edge_points(kernel):
             rv, rg = oracle.spherical_harmonics_grad(pts, l_max, normalized)
             assert np.all(np.isfinite(v)) and np.all(np.isfinite(g))
             assert_values(v, pts, l_max, normalized, F64_TOL, ref=rv)
-            assert_grads(g, pts, l_max, normalized, 1e-11, ref=rg)
+            assert_grads(g, pts, l_max, normalized, F64_TOL, ref=rg)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -211,7 +211,7 @@ def test_lanes_per_point_parity(lpp):
         rv, rg = oracle.spherical_harmonics_grad(x64, l_max, True)
         v, g = _run(x64, l_max, True, True, "degree", dtype=torch.float64, launch=lau)
         assert_values(v, x64, l_max, True, F64_TOL, ref=rv)
-        assert_grads(g, x64, l_max, True, F64_TOL * 10, ref=rg)
+        assert_grads(g, x64, l_max, True, F64_TOL, ref=rg)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
