@@ -295,6 +295,60 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ranks
+def launch_ranks(nproc: int) -> int:
+    """Runs this script with the same arguments as `nproc` ranks on this node
+    (torch.distributed.run, rendezvous on 127.0.0.1); returns their exit code."""
+    import socket
+
+    with socket.socket() as sock:
+        sock.bind(("127.0.0.1", 0))
+        port = sock.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={nproc}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", "--", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def rank_shard(n: int, rank: int, world: int):
+    """Weak scaling: the global cloud holds world * n points and rank r owns
+    the contiguous range shard.point_range gives it (n points each)."""
+    from paper_2302_08381_gb300 import shard
+
+    return shard.point_range(world * n, rank, world)
+
+
+def run_dry(args, rank, world):
+    """The multi-rank logic without a GPU: shard ranges, a gloo barrier around
+    stand-in timed steps, and the max over ranks, as the GPU arm does it."""
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("gloo")
+    start, end = rank_shard(args.n, rank, world)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        time.sleep(0.001 * (1 + rank))  # stand-in step; rank-dependent so the max is visible
+    step_ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([step_ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ranges = [None] * world
+        dist.all_gather_object(ranges, (start, end))
+    else:
+        ranges = [(start, end)]
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step_max": float(t.item()), "value": world * args.n / (float(t.item()) * 1e-3),
+                          "unit": "points/s (stand-in steps)", "scaling": "weak", "shards": ranges}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -312,13 +366,25 @@ def main():
                  "degree50_f64"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
+    ap.add_argument("--dry-run", action="store_true",
+                    help="host-only run of the multi-rank logic (gloo, no GPU): sharding, barrier, max over ranks")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: relaunch this script under torch.distributed.run
+        sys.exit(launch_ranks(args.gpus))
+
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and rank == 0:
+        print(f"bench.py: WORLD_SIZE={world} differs from --gpus {args.gpus}; running {world} rank(s)",
+              file=sys.stderr, flush=True)
+    if args.dry_run:
+        run_dry(args, rank, world)
+        return
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -359,6 +425,7 @@ def main():
 
     n, L = args.n, L_MAX
     K = (L + 1) ** 2
+    shard_start, shard_end = rank_shard(n, rank, world)
     xyz_np = inputs.shell_points(n, 0.5, 5.0, seed=8 + rank)
     xyz = torch.from_numpy(xyz_np).to(dev)
     sph = torch.empty((n, K), device=dev)
@@ -475,7 +542,8 @@ def main():
                 "l_max": L,
                 "outputs": f"sph [N,{K}] + dsph [N,3,{K}] FP32",
                 "l2": "flushed between timed launches (256 MB zero fill outside the timed events)",
-                "parallelism": f"points sharded, {world} independent rank(s)",
+                "parallelism": f"points sharded, {world} independent rank(s); rank 0 owns points "
+                f"[{shard_start}, {shard_end}) of {world * n} (contiguous ranges, no collective on the data path)",
                 "launch_shape": (
                     {"points_per_tile": tuned.points_per_tile, "warps_per_block": tuned.warps_per_block,
                      "blocks_per_sm": tuned.blocks_per_sm, "source": "sphericart_autotune"}

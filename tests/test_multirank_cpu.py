@@ -145,3 +145,26 @@ def test_two_rank_gloo_sharding_and_timing_reduction():
         assert t == 1.0  # max over ranks of 0.5 * (rank + 1)
         assert sets == list(range(64))
 
+
+
+def test_bench_launches_ranks_itself_dry_run():
+    """bench.py --gpus 2 starts two ranks on its own (torch.distributed.run,
+    gloo in the host-only dry run): both shard, barrier and reduce the max
+    time, and rank 0 prints one line with n_gpus = 2."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                             "MASTER_PORT")}
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--steps", "5",
+                          "--warmup", "3", "--n", "1000", "--dry-run"], capture_output=True, text=True, env=env,
+                         timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [json.loads(l) for l in res.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["dry_run"] and line["n_gpus"] == 2 and line["scaling"] == "weak"
+    assert line["shards"] == [[0, 1000], [1000, 2000]]
+    assert line["ms_per_step_max"] >= 2.0  # rank 1's stand-in steps (2 ms) set the max
