@@ -654,8 +654,9 @@ def _events_ms(torch, stream, fn, reps, flush=None):
 def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
     """512 ragged sets (sizes log-uniform in [1e3, 2e5], l_max from {3,6,8,12},
     N(0,1) FP32 points), values + gradients: the plan's persistent launches
-    (one per l_max class, and one for all sets; eager and replayed from a CUDA
-    graph) vs one launch per set (eager and captured in one graph)."""
+    (one per l_max class, and one for all sets), sphericart_compute_batched on
+    a device descriptor array (one launch), each eager and replayed from a
+    CUDA graph, vs one launch per set (eager and captured in one graph)."""
     sizes, lmax, xyz = inputs.ragged_sets(512, [3, 6, 8, 12], 1000, 200_000, seed=5)
     offs = np.concatenate([[0], np.cumsum(sizes)])
     xt = torch.from_numpy(xyz).to(dev)
@@ -677,7 +678,13 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
         arr, len(xs), stream.cuda_stream, 2, ctypes.byref(best), ctypes.byref(best_ms)))
     plan.close()
     plan = api.BatchPlan(xs, ls, launch=best, outputs=outs)  # one persistent launch per l_max class
-    one = api.BatchPlan(xs, ls, launch=best, outputs=outs, mode="one_launch")
+    one = api.BatchPlan(xs, ls, outputs=outs, mode="one_launch")
+    # the device-descriptor entry point: one launch over every set
+    desc = api.batch_descriptors(xs, ls, [o[0] for o in outs], [o[1] for o in outs])
+
+    def batched():
+        C.check("sphericart_compute_batched", C.lib().sphericart_compute_batched(
+            desc.data_ptr(), len(xs), C.SPH_BATCHED_GRADIENTS, stream.cuda_stream))
 
     def per_set():
         for x, L, o in zip(xs, ls, outs):
@@ -685,18 +692,23 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
 
     plan.execute()
     one.execute()
+    batched()
     per_set()
     torch.cuda.synchronize()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     g_plan = torch.cuda.CUDAGraph()
     g_one = torch.cuda.CUDAGraph()
+    g_batched = torch.cuda.CUDAGraph()
     g_sets = torch.cuda.CUDAGraph()
     with torch.cuda.stream(side):
         with torch.cuda.graph(g_plan, stream=side):
             plan.execute()
         with torch.cuda.graph(g_one, stream=side):
             one.execute()
+        with torch.cuda.graph(g_batched, stream=side):
+            C.check("sphericart_compute_batched", C.lib().sphericart_compute_batched(
+                desc.data_ptr(), len(xs), C.SPH_BATCHED_GRADIENTS, side.cuda_stream))
         with torch.cuda.graph(g_sets, stream=side):
             per_set()
     stream.wait_stream(side)
@@ -715,6 +727,8 @@ def run_batch_leg(torch, np, api, inputs, dev, stream, flush):
         ("persistent_per_lmax_graph", g_plan.replay),
         ("persistent_one_launch", one.execute),
         ("persistent_one_launch_graph", g_one.replay),
+        ("compute_batched_device_desc", batched),
+        ("compute_batched_device_desc_graph", g_batched.replay),
         ("per_set_launches", per_set),
         ("per_set_graph", g_sets.replay),
     ):
@@ -765,6 +779,12 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (200_000, 50, "l50_grad_f64_norm_n200k_degree_down",
          dict(gradients=True, normalized=True, kernel="degree_down"), 8, 4),
         (1_000_000, 16, "l16_grad_f64_n1M", dict(gradients=True), 8, 4),
+        # hard-coded l <= 3 + recursion (POINT_HC, AUTO's FP64 choice up to l_max 8
+        # with gradients, 3 for values) against the all-recursion POINT kernel
+        (1_000_000, 3, "l3_grad_f64_n1M_point", dict(gradients=True, kernel="point"), 8, 4),
+        (1_000_000, 3, "l3_grad_f64_n1M_point_hc", dict(gradients=True, kernel="point_hc"), 8, 4),
+        (4_194_304, 8, "l8_grad_f64_point", dict(gradients=True, kernel="point"), 8, 4),
+        (10_000, 8, "l8_values_f64_n10k_point_hc", dict(kernel="point_hc"), 8, 1),
     ):
         dt = torch.float64 if elem == 8 else torch.float32
         x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)

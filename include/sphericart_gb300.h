@@ -102,14 +102,20 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
  *           rows are staged in shared memory in windows of whole degrees and
  *           written with TMA bulk copies of 32-byte-aligned runs (~1 KB and
  *           longer, which GB300's HBM needs for full write bandwidth). Also a
- *           fused backward (sphericart_backward). */
+ *           fused backward (sphericart_backward).
+ *   POINT_HC: POINT with the degrees l <= min(l_max, 3) from generated
+ *           straight-line ("hard-coded") expressions and Eq. iter-q above
+ *           them, as the paper's GPU kernel does (Section 3.2; the hybrid of
+ *           Section 3.1, Table 1). l_max <= 8, values and gradients, FP32 or
+ *           FP64, same-type storage. */
 typedef enum {
     SPH_KERNEL_AUTO = 0,
     SPH_KERNEL_POINT = 1,
     SPH_KERNEL_SLICE = 2,
     SPH_KERNEL_DEGREE = 3,
     SPH_KERNEL_DEGREE_DOWN = 4,
-    SPH_KERNEL_ROW = 5
+    SPH_KERNEL_ROW = 5,
+    SPH_KERNEL_POINT_HC = 6
 } sph_kernel;
 
 #define SPH_MAX_L 128
@@ -260,8 +266,12 @@ int sphericart_batch_plan_create(const sph_batch_set* sets, int nsets,
  *                        shared-memory size fitted to that l_max's tile (the
  *                        default of sphericart_batch_plan_create; measured faster
  *                        on GB300)
- *   SPH_BATCH_ONE_LAUNCH one persistent launch for every set, branching on each
- *                        tile's l_max, shared memory sized for the largest tile */
+ *   SPH_BATCH_ONE_LAUNCH one persistent launch for every set (one per
+ *                        combination of gradients / normalized present),
+ *                        the kernel of sphericart_compute_batched: the sets
+ *                        sorted by l_max in shared memory, a switch over the
+ *                        compile-time l_max bodies, per-l_max tiles filling
+ *                        one shared-memory budget per warp */
 typedef enum { SPH_BATCH_PER_LMAX = 0, SPH_BATCH_ONE_LAUNCH = 1 } sph_batch_mode;
 
 /* sphericart_batch_plan_create_ex: sphericart_batch_plan_create with a mode
@@ -282,8 +292,52 @@ int sphericart_batch_plan_destroy(sph_batch_plan* plan);
 int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points,
                                int64_t* total_tiles);
 
+/* Flags of sphericart_compute_batched: every set of one call has the same. */
+typedef enum { SPH_BATCHED_GRADIENTS = 1, SPH_BATCHED_NORMALIZED = 2 } sph_batched_flags;
+
+/* sphericart_compute_batched: a ragged batch in ONE persistent launch, from a
+ * descriptor array in DEVICE memory (the paper's problem, "all (l,m) up to
+ * l_max, possibly for many points", Section 3, for many point sets at once;
+ * the batched form addresses the under-filled GPU at small point counts noted
+ * with Table 3).
+ *   desc   DEVICE (or managed / page-locked host) array of nsets sph_batch_set,
+ *          read by the kernel: the caller may fill it on the GPU and replay a
+ *          captured call with new sizes. Per set: xyz [n,3] f32, sph
+ *          [n,(l_max+1)^2] f32, dsph [n,3,(l_max+1)^2] f32 (non-NULL exactly
+ *          when flags has SPH_BATCHED_GRADIENTS), n >= 0, 0 <= l_max <= 16,
+ *          normalized equal to (flags & SPH_BATCHED_NORMALIZED) != 0, buffers
+ *          4-byte aligned (16 for the bulk-store path). A set with n = 0 is
+ *          skipped whatever its pointers and flags.
+ *   nsets  >= 0 (0: no-op). Arrays longer than 2048 sets run as one launch
+ *          per 2048 sets.
+ *   flags  SPH_BATCHED_GRADIENTS | SPH_BATCHED_NORMALIZED.
+ * Each block (one per SM) sorts the sets by l_max in shared memory, then
+ * runs the l_max classes present one after the other, each with its
+ * compile-time body, the single-set POINT tile of that l_max and as many
+ * warps as its staging buffers fit in the block's shared memory; warps take
+ * tiles from per-class counters that the kernel returns to zero itself (a
+ * ring of 256 static counter sets per device and flag combination: at most
+ * 256 calls may be in flight at once on one device). Sets whose descriptor is invalid are
+ * skipped and the value 2 is OR-ed into the device status word (see
+ * sphericart_device_status); the host cannot read device descriptors, so
+ * these checks happen on the GPU. Capturable in a CUDA graph once a first
+ * call on the device has run eagerly (it sets the kernel's shared-memory
+ * attribute and allocates the status word). Errors: SPH_EINVAL for nsets <
+ * 0, unknown flags, a NULL or pageable desc; SPH_ECUDA on a launch failure. */
+int sphericart_compute_batched(const sph_batch_set* desc, int nsets, int flags, void* stream);
+
+/* sphericart_compute_batched_ex: with a launch shape (NULL = default):
+ * points_per_tile = tiles that fit this many l_max = 8 value+gradient rows
+ * (1,296 bytes each; 0 = the single-set POINT tile of each l_max),
+ * warps_per_block in [0,16] caps the warps of a block (0 = 16), blocks_per_sm
+ * (0 = occupancy). */
+int sphericart_compute_batched_ex(const sph_batch_set* desc, int nsets, int flags,
+                                  const sph_launch* launch, void* stream);
+
 /* sphericart_batch_compute_noalloc: evaluates a ragged batch like a plan does,
- * in one persistent launch on `stream`, without allocating any device memory.
+ * with the one-launch kernel of sphericart_compute_batched (one launch per
+ * combination of gradients / normalized present) on `stream`, without
+ * allocating any device memory.
  * It exists for callers that cannot call cudaMalloc -- code whose device
  * memory is owned by a fixed arena or a framework allocator, or code that
  * cannot afford the device synchronisation cudaMalloc implies. (The paper has
@@ -291,13 +345,18 @@ int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points
  *   sets / nsets  as for sphericart_batch_plan_create (HOST array, read during
  *                 the call only); at most 4096 sets, more returns SPH_EINVAL.
  *   launch        NULL or a shape, as for sphericart_batch_plan_create.
- * The work list and the tile counter live in a static device array of the
- * library (about 225 KB on every GPU that loads it, held until exit). The
+ * The descriptors are copied into a static device array of the library
+ * (160 KB on every GPU that loads it, held until exit); the tile counters
+ * are the self-resetting static ring of sphericart_compute_batched. The
  * first call on a device looks up that array's address (set-up); make that
- * first call before any stream capture. Every call reuses the same array:
- * the counter is cleared on each call, and calls whose work overlaps on the
- * GPU (different streams, or host threads racing) race on it -- serialise
- * them. Output buffers are the caller's, as everywhere. */
+ * first call before any stream capture. The address is kept for the life of
+ * the process: after cudaDeviceReset (or anything else that replaces the
+ * device's primary context) this entry point must not be called again.
+ * Every call reuses the same array, and calls whose work overlaps on the GPU
+ * (different streams, or host threads racing) race on it -- serialise them. The work list is staged in host
+ * memory that the next call overwrites, so the call refuses a stream that is
+ * being captured (SPH_EINVAL, nothing enqueued). Output buffers are the
+ * caller's, as everywhere. */
 int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int nsets,
                                      const sph_launch* launch, void* stream);
 
@@ -327,7 +386,8 @@ int sphericart_max_l(int dtype, int qprec, int kernel);
 int sphericart_host_table(int l_max, int which, double* out);
 
 /* sphericart_device_status: reads and clears the device-side status word of
- * the current device (nonzero = a bounded wait timed out inside a kernel).
+ * the current device, an OR of: 1 = a bounded wait timed out inside a kernel,
+ * 2 = sphericart_compute_batched skipped a set with an invalid descriptor.
  * Synchronises the device. Returns SPH_OK and writes the word to *status. */
 int sphericart_device_status(uint32_t* status);
 

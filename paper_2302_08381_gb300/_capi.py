@@ -19,7 +19,9 @@ SPH_OUT_SAME, SPH_OUT_BF16 = 0, 1
 SPH_Q_NATIVE, SPH_Q_F64 = 0, 1
 SPH_KERNEL_AUTO, SPH_KERNEL_POINT, SPH_KERNEL_SLICE, SPH_KERNEL_DEGREE, SPH_KERNEL_DEGREE_DOWN, SPH_KERNEL_ROW = (
     0, 1, 2, 3, 4, 5)
+SPH_KERNEL_POINT_HC = 6
 SPH_BATCH_PER_LMAX, SPH_BATCH_ONE_LAUNCH = 0, 1
+SPH_BATCHED_GRADIENTS, SPH_BATCHED_NORMALIZED = 1, 2
 SPH_MAX_L = 128
 SPH_MAX_L_POINT = 16
 
@@ -80,6 +82,8 @@ _PROTOS = {
     "sphericart_batch_plan_destroy": (_I, [_P]),
     "sphericart_batch_plan_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "sphericart_batch_compute_noalloc": (_I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), _P]),
+    "sphericart_compute_batched": (_I, [_P, _I, _I, _P]),
+    "sphericart_compute_batched_ex": (_I, [_P, _I, _I, ctypes.POINTER(sph_launch), _P]),
     "sphericart_last_error": (ctypes.c_char_p, []),
     "sphericart_max_l": (_I, [_I, _I, _I]),
     "sphericart_host_table": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),

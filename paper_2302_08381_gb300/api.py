@@ -16,6 +16,7 @@ _KERNELS = {
     "degree": C.SPH_KERNEL_DEGREE,
     "degree_down": C.SPH_KERNEL_DEGREE_DOWN,
     "row": C.SPH_KERNEL_ROW,
+    "point_hc": C.SPH_KERNEL_POINT_HC,
 }
 _QPREC = {"native": C.SPH_Q_NATIVE, "f64": C.SPH_Q_F64}
 
@@ -274,6 +275,51 @@ def load_tuning(path: str) -> int:
 def device_status() -> int:
     """Reads and clears the device status word (nonzero: a bounded wait timed out)."""
     return C.sphericart_device_status()
+
+
+def batch_descriptors(xyz_list, lmax_list, sph_list, dsph_list, normalized=False, device=None):
+    """sph_batch_set descriptors of point sets as a CUDA uint8 tensor [nsets, 40]
+    (the device array ``sphericart_compute_batched`` reads)."""
+    n = len(xyz_list)
+    arr = (C.sph_batch_set * n)()
+    for i in range(n):
+        x, s, d = xyz_list[i], sph_list[i], dsph_list[i] if dsph_list is not None else None
+        arr[i] = C.sph_batch_set(x.data_ptr(), s.data_ptr(), d.data_ptr() if d is not None else None, x.shape[0],
+                                 int(lmax_list[i]), 1 if normalized else 0)
+    host = torch.frombuffer(bytearray(arr), dtype=torch.uint8).view(n, -1)
+    return host.to(device or xyz_list[0].device)
+
+
+def compute_batched(xyz_list, lmax_list, normalized=False, gradients=True, outputs=None, launch=None):
+    """Ragged point sets (CUDA float32 [n_s, 3], l_max_s <= 16) in one persistent
+    launch (``sphericart_compute_batched``) on torch's current stream.
+
+    Returns ``(sph_list, dsph_list)`` (``dsph_list`` None without gradients);
+    ``outputs`` may supply them as a list of (sph, dsph) pairs.
+    """
+    if len(xyz_list) != len(lmax_list) or not xyz_list:
+        raise ValueError("need one l_max per point set")
+    dev = xyz_list[0].device
+    sph_list, dsph_list = [], [] if gradients else None
+    for i, (x, L) in enumerate(zip(xyz_list, lmax_list)):
+        _check_points(x)
+        if x.dtype != torch.float32:
+            raise TypeError("batched sets are float32")
+        K = n_columns(int(L))
+        if outputs is not None:
+            s, d = outputs[i]
+        else:
+            s = torch.empty((x.shape[0], K), device=dev)
+            d = torch.empty((x.shape[0], 3, K), device=dev) if gradients else None
+        sph_list.append(s)
+        if gradients:
+            dsph_list.append(d)
+    desc = batch_descriptors(xyz_list, lmax_list, sph_list, dsph_list, normalized, dev)
+    flags = (C.SPH_BATCHED_GRADIENTS if gradients else 0) | (C.SPH_BATCHED_NORMALIZED if normalized else 0)
+    C.check("sphericart_compute_batched_ex",
+            C.lib().sphericart_compute_batched_ex(desc.data_ptr(), len(xyz_list), flags, _launch(launch),
+                                                  _stream(dev)))
+    return sph_list, dsph_list
 
 
 class BatchPlan:

@@ -24,11 +24,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <numeric>
 #include <vector>
 
 #include "sph_batch.cuh"
+#include "sph_batch_one.cuh"
 
 namespace sph {
 
@@ -55,6 +58,148 @@ int batch_run(const BatchLaunch& b, const BatchSet* sets, unsigned long long* co
     return b.L >= 0 ? batch_class_fn(b.L)(a) : batch_kernel_run<-1, -1>(a);
 }
 
+namespace {
+
+int tile_mult4(int L) {
+    const int K = (L + 1) * (L + 1);
+    const int r = (K * 4) % 16;
+    return r == 0 ? 1 : 16 / (r == 8 ? 8 : 4);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ one launch
+// Shapes of the one-launch kernel for one flag class and one chunk of
+// descriptors: per l_max the single-set POINT tile (tuned if installed) or,
+// with `budget_rows` > 0, the tile that fits that many l_max = 8
+// value+gradient rows (1,296 bytes each); the warps of a block that run that
+// class (as many staging buffers as the block's shared memory holds, at most
+// `max_warps`); the block's warps and staging bytes (the largest class).
+struct OneShapes {
+    OneClass cls[SPH_MAX_L_POINT + 1];
+    int staging_bytes = 0;
+    int W = 1;
+};
+
+int one_shapes(int grad, const sph_launch& lau, int nsets, OneShapes* out) {
+    OneShapes o;
+    const int max_warps = lau.warps_per_block > 0 ? std::min(lau.warps_per_block, kOneMaxWarps) : kOneMaxWarps;
+    const size_t optin = size_t(max_smem_optin());
+    const size_t reserve = one_table_bytes(nsets) + 1024;  // the work table, static shared memory
+    if (optin <= reserve) {
+        set_error("batch one-launch: no shared memory left for staging");
+        return SPH_EINVAL;
+    }
+    const size_t S = (optin - reserve) / 128 * 128;
+    for (int L = 0; L <= SPH_MAX_L_POINT; ++L) {
+        const int K = (L + 1) * (L + 1);
+        const int V = (K % 2 == 0) ? K + 1 : K;
+        const int D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;
+        const int mult = tile_mult4(L);
+        int P;
+        if (lau.points_per_tile > 0) {
+            const int row = 4 * (V + (grad ? D : 0));
+            P = std::min(kOneMaxTile, lau.points_per_tile * 1296 / row) / mult * mult;
+        } else {
+            P = point_fwd_shape(L, grad).points_per_tile;
+        }
+        P = std::max(P, mult);
+        const size_t bytes = align128(size_t(P) * V * 4) + (grad ? align128(size_t(P) * D * 4) : 0);
+        const int W = int(std::min<size_t>(size_t(max_warps), S / bytes));
+        if (W < 1) {
+            set_error("batch one-launch: a %d-point tile at l_max %d needs %zu bytes of shared memory", P, L, bytes);
+            return SPH_EINVAL;
+        }
+        o.cls[L] = OneClass{P, int(bytes), W, 0};
+        o.W = std::max(o.W, W);
+        o.staging_bytes = std::max(o.staging_bytes, int(size_t(W) * bytes));
+    }
+    o.staging_bytes = std::max(o.staging_bytes, int(align128(one_scratch_bytes(nsets))));
+    *out = o;
+    return SPH_OK;
+}
+
+// Resolved launch of one chunk of <= kOneMaxSets descriptors.
+struct OneRec {
+    int gn = 0;
+    int off = 0;  // first descriptor of the chunk
+    int cnt = 0;
+    int blocks = 1;
+    size_t smem = 0;
+    OneShapes sh;
+};
+
+// Shapes, shared memory and grid of a chunk; returns SPH_OK or an error code
+// with the message set.
+int one_resolve(OneRec& r, const sph_launch& lau) {
+    int st = one_shapes(r.gn & 1, lau, r.cnt, &r.sh);
+    if (st != SPH_OK) return st;
+    r.smem = size_t(r.sh.staging_bytes) + one_table_bytes(r.cnt);
+    // Shared-memory attribute and occupancy, once per (device, flags, warps,
+    // bytes): later calls (e.g. under stream capture) make no such query.
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, size_t>, int> cache;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch one-launch: no usable CUDA device");
+        return SPH_ECUDA;
+    }
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto key = std::make_tuple(dev, r.gn, r.sh.W, r.smem);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            occ = it->second;
+        } else {
+            OneArgs q{};
+            q.W = r.sh.W;
+            q.smem = r.smem;
+            q.occ_out = &occ;
+            const int e = batch_one_fn(r.gn)(q);
+            if (e != 0) {
+                set_error("batch one-launch: %s", cudaGetErrorString(static_cast<cudaError_t>(e)));
+                return SPH_ECUDA;
+            }
+            cache[key] = occ;
+        }
+    }
+    if (occ <= 0) {
+        set_error("batch one-launch: a block of %d warps with %zu bytes of shared memory does not fit an SM",
+                  r.sh.W, r.smem);
+        return SPH_EINVAL;
+    }
+    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, occ) : occ;
+    r.blocks = std::max(1, bps * sm_count());
+    return SPH_OK;
+}
+
+int one_launch(const OneRec& r, const sph_batch_set* desc, OneCounter* ctr, uint32_t* status, void* stream) {
+    OneArgs a{};
+    a.desc = desc + r.off;
+    a.nsets = r.cnt;
+    a.ctr = ctr;
+    a.staging_bytes = r.sh.staging_bytes;
+    a.W = r.sh.W;
+    a.blocks = r.blocks;
+    a.smem = r.smem;
+    a.cls = r.sh.cls;
+    a.status = status;
+    a.stream = stream;
+    return batch_one_fn(r.gn)(a);
+}
+
+bool one_launch_shape_ok(const sph_launch& lau) {
+    if (lau.warps_per_block < 0 || lau.warps_per_block > kOneMaxWarps || lau.points_per_tile < 0 ||
+        lau.points_per_tile > 160 || lau.blocks_per_sm < 0 || lau.blocks_per_sm > 32) {
+        set_error("batch launch: warps_per_block in [0,%d], points_per_tile (budget rows) in [0,160], "
+                  "blocks_per_sm in [0,32]", kOneMaxWarps);
+        return false;
+    }
+    return true;
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -68,14 +213,71 @@ struct sph_batch_plan {
     BatchSet* d_sets = nullptr;
     unsigned long long* d_counter = nullptr;  // one counter per launch
     std::vector<BatchLaunch> launches;
+    // SPH_BATCH_ONE_LAUNCH: descriptors grouped by flag class, one launch per
+    // chunk of <= kOneMaxSets sets of one class (usually a single launch)
+    sph_batch_set* d_desc = nullptr;
+    OneCounter* d_one_ctr = nullptr;
+    std::vector<OneRec> one;
 };
 
 namespace {
 
-int tile_mult4(int L) {
-    const int K = (L + 1) * (L + 1);
-    const int r = (K * 4) % 16;
-    return r == 0 ? 1 : 16 / (r == 8 ? 8 : 4);
+int gn_of_set(const sph_batch_set& s) { return (s.dsph ? 1 : 0) + (s.normalized ? 2 : 0); }
+
+// SPH_BATCH_ONE_LAUNCH plans: the descriptors (validated by the caller)
+// grouped by flag class in a device array, one launch per chunk of one class.
+int plan_create_one(const sph_batch_set* sets, int nsets, const sph_launch& lau, int dev, sph_batch_plan** out) {
+    if (!one_launch_shape_ok(lau)) return SPH_EINVAL;
+    auto* plan = new sph_batch_plan();
+    plan->device = dev;
+    plan->nsets = nsets;
+    plan->mode = SPH_BATCH_ONE_LAUNCH;
+    bool need[4] = {false, false, false, false};
+    for (int i = 0; i < nsets; ++i) need[gn_of_set(sets[i])] = true;
+    std::vector<sph_batch_set> hs;
+    hs.reserve(nsets);
+    for (int g = 0; g < 4; ++g) {
+        if (!need[g]) continue;
+        const int off0 = int(hs.size());
+        for (int i = 0; i < nsets; ++i)
+            if (gn_of_set(sets[i]) == g) hs.push_back(sets[i]);
+        for (int c = off0; c < int(hs.size()); c += kOneMaxSets) {
+            OneRec r;
+            r.gn = g;
+            r.off = c;
+            r.cnt = std::min(kOneMaxSets, int(hs.size()) - c);
+            const int st = one_resolve(r, lau);
+            if (st != SPH_OK) {
+                delete plan;
+                return st;
+            }
+            for (int i = r.off; i < r.off + r.cnt; ++i) {
+                plan->total_points += hs[i].n;
+                const int P = r.sh.cls[hs[i].l_max].P;
+                plan->total_tiles += (hs[i].n + P - 1) / P;
+            }
+            plan->one.push_back(r);
+        }
+    }
+    if (cudaMalloc(&plan->d_desc, sizeof(sph_batch_set) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&plan->d_one_ctr, sizeof(OneCounter) * plan->one.size()) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(plan->d_desc);
+        delete plan;
+        set_error("batch plan: device allocation failed");
+        return SPH_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(plan->d_desc, hs.data(), sizeof(sph_batch_set) * hs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_one_ctr, 0, sizeof(OneCounter) * plan->one.size());
+    if (e != cudaSuccess) {
+        cudaFree(plan->d_desc);
+        cudaFree(plan->d_one_ctr);
+        delete plan;
+        set_error("batch plan: %s", cudaGetErrorString(e));
+        return SPH_ECUDA;
+    }
+    *out = plan;
+    return SPH_OK;
 }
 
 }  // namespace
@@ -117,6 +319,7 @@ int sphericart_batch_plan_create_ex(const sph_batch_set* sets, int nsets, const 
         return SPH_ECUDA;
     }
     sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
+    if (mode == SPH_BATCH_ONE_LAUNCH) return plan_create_one(sets, nsets, lau, dev, plan_out);
     const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
     if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 160) {
         set_error("warps_per_block=%d must be in [1,8], points_per_tile (budget rows) in [0,160]", W);
@@ -241,8 +444,24 @@ int sphericart_batch_execute(const sph_batch_plan* plan, void* stream) {
         set_error("batch_execute: plan is NULL");
         return SPH_EINVAL;
     }
-    if (plan->launches.empty()) return SPH_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!plan->one.empty()) {
+        // The kernels return their counters to zero themselves; the reset
+        // here only guards against a previous run that did not finish.
+        cudaError_t e = cudaMemsetAsync(plan->d_one_ctr, 0, sizeof(OneCounter) * plan->one.size(), st);
+        uint32_t* status = device_status_word();
+        for (size_t i = 0; i < plan->one.size() && e == cudaSuccess; ++i) {
+            const OneRec& r = plan->one[i];
+            e = static_cast<cudaError_t>(
+                one_launch(r, plan->d_desc, plan->d_one_ctr + i, status, stream));
+        }
+        if (e != cudaSuccess) {
+            set_error("batch_execute: %s", cudaGetErrorString(e));
+            return SPH_ECUDA;
+        }
+        return SPH_OK;
+    }
+    if (plan->launches.empty()) return SPH_OK;
     cudaError_t e =
         cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long) * plan->launches.size(), st);
     for (size_t i = 0; i < plan->launches.size() && e == cudaSuccess; ++i)
@@ -263,9 +482,54 @@ int sphericart_batch_plan_destroy(sph_batch_plan* plan) {
     cudaDeviceSynchronize();
     cudaFree(plan->d_sets);
     cudaFree(plan->d_counter);
+    cudaFree(plan->d_desc);
+    cudaFree(plan->d_one_ctr);
     if (cur >= 0) cudaSetDevice(cur);
     delete plan;
     return SPH_OK;
+}
+
+// ------------------------------------------------- device descriptor array
+int sphericart_compute_batched_ex(const sph_batch_set* desc, int nsets, int flags, const sph_launch* launch,
+                                  void* stream) {
+    if (nsets < 0 || (flags & ~(SPH_BATCHED_GRADIENTS | SPH_BATCHED_NORMALIZED)) != 0) {
+        set_error("compute_batched: nsets=%d must be >= 0 and flags=%d a combination of SPH_BATCHED_*", nsets, flags);
+        return SPH_EINVAL;
+    }
+    if (nsets == 0) return SPH_OK;
+    if (!desc || reinterpret_cast<uintptr_t>(desc) % alignof(sph_batch_set) != 0) {
+        set_error("compute_batched: desc must be a non-NULL, %zu-byte aligned device array",
+                  alignof(sph_batch_set));
+        return SPH_EINVAL;
+    }
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, desc) != cudaSuccess || attr.type == cudaMemoryTypeUnregistered) {
+        cudaGetLastError();
+        set_error("compute_batched: desc must be device, managed or page-locked host memory");
+        return SPH_EINVAL;
+    }
+    const sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
+    if (!one_launch_shape_ok(lau)) return SPH_EINVAL;
+    const int gn = flags & 3;
+    uint32_t* status = device_status_word();
+    for (int c = 0; c < nsets; c += kOneMaxSets) {
+        OneRec r;
+        r.gn = gn;
+        r.off = c;
+        r.cnt = std::min(kOneMaxSets, nsets - c);
+        const int st = one_resolve(r, lau);
+        if (st != SPH_OK) return st;
+        const int e = one_launch(r, desc, nullptr, status, stream);
+        if (e != 0) {
+            set_error("compute_batched launch: %s", cudaGetErrorString(static_cast<cudaError_t>(e)));
+            return SPH_ECUDA;
+        }
+    }
+    return SPH_OK;
+}
+
+int sphericart_compute_batched(const sph_batch_set* desc, int nsets, int flags, void* stream) {
+    return sphericart_compute_batched_ex(desc, nsets, flags, nullptr, stream);
 }
 
 int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points, int64_t* total_tiles) {
@@ -287,24 +551,24 @@ int sphericart_batch_plan_info(const sph_batch_plan* plan, int64_t* total_points
 // allocator that must not be bypassed), or code on a latency-critical path
 // where cudaMalloc's implicit device synchronisation is not acceptable.
 //
-// The work list and the tile counter live in the file-scope array below
-// instead of a plan's cudaMalloc'd buffers. Every GPU that loads this
-// library holds kNoAllocScratchBytes (about 225 KB) of it until the process
+// The descriptors are copied into the file-scope array below instead of a
+// plan's cudaMalloc'd buffer, and the one-launch kernel runs on them with a
+// self-resetting tile counter from its static ring. Every GPU that loads
+// this library holds kNoAllocScratchBytes (160 KB) of it until the process
 // exits. All calls on a device share it and it keeps the last call's
-// contents; the counter is cleared on every call.
+// descriptors.
 namespace sph {
 namespace {
 
 constexpr int kNoAllocMaxSets = 4096;
-constexpr size_t kNoAllocCounterBytes = 256;  // counter, padded to keep the sets 256-byte aligned
-constexpr size_t kNoAllocScratchBytes = kNoAllocCounterBytes + sizeof(BatchSet) * kNoAllocMaxSets;
+constexpr size_t kNoAllocScratchBytes = sizeof(sph_batch_set) * kNoAllocMaxSets;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;                            // guards the two arrays below
 void* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};   // device address of g_noalloc_scratch, per device
-BatchSet g_noalloc_host[kNoAllocMaxSets];           // host staging of the work list
+sph_batch_set g_noalloc_host[kNoAllocMaxSets];      // host staging of the descriptors
 
 }  // namespace
 }  // namespace sph
@@ -339,10 +603,22 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         }
     }
     const sph_launch lau = launch ? *launch : sph_launch{0, 0, 0, 0};
-    const int W = lau.warps_per_block > 0 ? lau.warps_per_block : 1;
-    if (W > 8 || lau.points_per_tile < 0 || lau.points_per_tile > 160 || lau.blocks_per_sm < 0) {
-        set_error("batch_compute_noalloc: bad launch shape");
-        return SPH_EINVAL;
+    if (!one_launch_shape_ok(lau)) return SPH_EINVAL;
+    // The descriptors are copied from host staging that the next call
+    // overwrites; a captured copy would read it again at every replay.
+    // So a stream that is being captured is refused before anything is
+    // enqueued or set up.
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t qe = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+        if (qe != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            if (qe != cudaSuccess) cudaGetLastError();
+            set_error("batch_compute_noalloc: the stream is being captured (or its capture state is unknown: %s); "
+                      "this entry point stages its work list in host memory that later calls overwrite, so it "
+                      "runs eagerly only",
+                      qe != cudaSuccess ? cudaGetErrorString(qe) : "capturing");
+            return SPH_EINVAL;
+        }
     }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
@@ -350,7 +626,6 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         set_error("batch_compute_noalloc: no usable CUDA device");
         return SPH_ECUDA;
     }
-    const int budget = lau.points_per_tile > 0 ? lau.points_per_tile * 1296 : 32 * 1296;
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     // Set-up, once per device, with that device current: the device address
@@ -365,75 +640,35 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         }
         g_noalloc_dev_ptr[dev] = p;
     }
-    unsigned char* base = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
-    unsigned long long* d_counter = reinterpret_cast<unsigned long long*>(base);
-    BatchSet* d_sets = reinterpret_cast<BatchSet*>(base + kNoAllocCounterBytes);
+    sph_batch_set* d_sets = static_cast<sph_batch_set*>(g_noalloc_dev_ptr[dev]);
 
-    // Work list in host staging: sets grouped by decreasing l_max (a
-    // counting sort, no allocation), tile prefix sums as in the plans.
-    int count[SPH_MAX_L_POINT + 2] = {0};
-    for (int i = 0; i < nsets; ++i) ++count[SPH_MAX_L_POINT - sets[i].l_max + 1];
-    for (int b = 1; b <= SPH_MAX_L_POINT + 1; ++b) count[b] += count[b - 1];
-    int64_t tiles = 0;
-    int max_bytes = 0;
-    for (int i = 0; i < nsets; ++i) {
-        const sph_batch_set& s = sets[i];
-        const int L = s.l_max;
-        const int K = (L + 1) * (L + 1);
-        const int grad = s.dsph ? 1 : 0;
-        const int V = (K % 2 == 0) ? K + 1 : K, D = (K % 2 == 0) ? 3 * K + 1 : 3 * K;  // smem row strides
-        const int row = 4 * (V + (grad ? D : 0));
-        const int mult = tile_mult4(L);
-        int P = std::min(kBatchMaxTile, std::max(1, budget / row));
-        P = std::max(mult, P / mult * mult);
-        const int bytes = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
-        max_bytes = std::max(max_bytes, bytes);
-        BatchSet& b = g_noalloc_host[count[SPH_MAX_L_POINT - L]++];
-        b = BatchSet{};
-        b.xyz = s.xyz;
-        b.sph = s.sph;
-        b.dsph = s.dsph;
-        b.n = s.n;
-        b.L = L;
-        b.P = P;
-        b.norm = s.normalized ? 1 : 0;
-        b.bulk = (reinterpret_cast<uintptr_t>(s.sph) % 16 == 0 && reinterpret_cast<uintptr_t>(s.dsph) % 16 == 0) ? 1 : 0;
-    }
-    for (int i = 0; i < nsets; ++i) {
-        g_noalloc_host[i].tile_begin = tiles;
-        tiles += (g_noalloc_host[i].n + g_noalloc_host[i].P - 1) / g_noalloc_host[i].P;
-    }
-    if (tiles == 0) return SPH_OK;
-    const size_t smem = size_t(W) * size_t(max_bytes);
-    if (smem > size_t(max_smem_optin())) {
-        set_error("batch_compute_noalloc: needs %zu bytes of shared memory per block", smem);
-        return SPH_EINVAL;
-    }
+    // Descriptors grouped by flag class (gradients, normalized), stable.
+    int count[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < nsets; ++i) ++count[gn_of_set(sets[i]) + 1];
+    for (int g = 1; g <= 4; ++g) count[g] += count[g - 1];
+    int start[4] = {count[0], count[1], count[2], count[3]};
+    for (int i = 0; i < nsets; ++i) g_noalloc_host[count[gn_of_set(sets[i])]++] = sets[i];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // From pageable host memory the copy has consumed g_noalloc_host when it
     // returns, so the staging may be reused by the next call.
-    cudaError_t e = cudaMemcpyAsync(d_sets, g_noalloc_host, sizeof(BatchSet) * size_t(nsets), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
-    BatchLaunch bl;  // one launch for every l_max, as SPH_BATCH_ONE_LAUNCH
-    bl.W = W;
-    bl.set_begin = 0;
-    bl.set_end = nsets;
-    bl.tile_begin = 0;
-    bl.tile_end = tiles;
-    bl.per_warp_bytes = max_bytes;
-    bl.smem = smem;
-    int occ = 1;
-    if (e == cudaSuccess) e = static_cast<cudaError_t>(batch_run(bl, d_sets, d_counter, stream, &occ));
+    cudaError_t e =
+        cudaMemcpyAsync(d_sets, g_noalloc_host, sizeof(sph_batch_set) * size_t(nsets), cudaMemcpyHostToDevice, st);
+    for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
+        const int end = g < 3 ? start[g + 1] : nsets;
+        if (end == start[g]) continue;
+        for (int c = start[g]; c < end && e == cudaSuccess; c += kOneMaxSets) {
+            OneRec r;
+            r.gn = g;
+            r.off = c;
+            r.cnt = std::min(kOneMaxSets, end - c);
+            const int rs = one_resolve(r, lau);
+            if (rs != SPH_OK) return rs;
+            e = static_cast<cudaError_t>(one_launch(r, d_sets, nullptr, nullptr, stream));
+        }
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("batch_compute_noalloc: %s", cudaGetErrorString(e));
-        return SPH_ECUDA;
-    }
-    const int bps = lau.blocks_per_sm > 0 ? std::min(lau.blocks_per_sm, occ) : occ;
-    bl.blocks = int(std::max<int64_t>(1, std::min<int64_t>((tiles + W - 1) / W, int64_t(bps) * sm_count())));
-    e = static_cast<cudaError_t>(batch_run(bl, d_sets, d_counter, stream, nullptr));
-    if (e != cudaSuccess) {
-        set_error("batch_compute_noalloc launch: %s", cudaGetErrorString(e));
         return SPH_ECUDA;
     }
     return SPH_OK;

@@ -155,6 +155,55 @@ const void* device_tables_down(int dtype) {
     });
 }
 
+// Coefficient streams of the ROW kernels (FP32): entry (d * 8 + k) * 8 + j
+// holds, for degree d and channel m = j + 8k (lane j, slot k), the float4
+// {A, B, S, e} of the packed tables and, in a second array after the first,
+// f; zero where m > d. At m = 0, e and f are given WITHOUT the 1/sqrt2 of the
+// m = 0 column (the kernel applies it through c_0).
+const void* device_row_tables() {
+    const int d = current_device();
+    if (d < 0) {
+        set_error("no current CUDA device");
+        return nullptr;
+    }
+    static void* slots[kMaxDevices] = {nullptr};
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (slots[d]) return slots[d];
+    const HostTables& h = host_tables();
+    constexpr int kEntries = kRowLanes * kRowDegrees * kRowSlots;
+    std::vector<float> host(size_t(kEntries) * 5, 0.f);
+    float* a4 = host.data();
+    float* f1 = host.data() + size_t(kEntries) * 4;
+    for (int j = 0; j < kRowLanes; ++j)
+        for (int l = 0; l < kRowDegrees; ++l)
+            for (int k = 0; k < kRowSlots; ++k) {
+                const int m = j + kRowLanes * k;
+                if (m > l) continue;
+                const int i = tri(l, m);
+                const size_t o = (size_t(l) * kRowSlots + k) * kRowLanes + j;
+                const double unfold = (m == 0) ? 1.0 / h.inv_sqrt2 : 1.0;
+                a4[4 * o + 0] = float(m <= l - 2 ? h.a[i] : (m == l - 1 ? h.d[i] : 0.0));
+                a4[4 * o + 1] = float(m <= l - 2 ? h.b[i] : 0.0);
+                a4[4 * o + 2] = float(m == l ? h.qll[i] : 0.0);
+                a4[4 * o + 3] = float(h.e[i] * unfold);
+                f1[o] = float(h.fz[i] * unfold);
+            }
+    void* p = nullptr;
+    if (cudaMalloc(&p, host.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of the ROW tables failed");
+        return nullptr;
+    }
+    if (cudaMemcpy(p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        set_error("upload of the ROW tables failed");
+        return nullptr;
+    }
+    slots[d] = p;
+    return p;
+}
+
 uint32_t* device_status_word() {
     const int d = current_device();
     if (d < 0) return nullptr;
@@ -322,6 +371,18 @@ int degree_default_lpp(int l_max, int dtype, int qprec) {
     return 4;
 }
 
+}  // namespace
+
+// FP64 (FP64-pipe bound): the hybrid with hard-coded l <= 3 runs fewer FP64
+// instructions; measured 1.07-2.3x faster with gradients up to l_max 8 and
+// 1.2-1.5x for values up to l_max 3, equal or slower beyond. In FP32 (bound
+// by HBM writes) it makes no difference.
+bool point_hybrid_wins(int l_max, int dtype, bool grad) {
+    return dtype == SPH_F64 && (grad ? l_max <= kHcMaxL : l_max <= 3);
+}
+
+namespace {
+
 // AUTO kernel family of a forward request (measured on GB300). POINT
 // (compile-time l_max, TMA bulk stores) wins whenever it applies in FP32, and
 // in FP64 up to l_max ~ 10; beyond that FP64 arithmetic (FP64 inputs or the
@@ -329,9 +390,10 @@ int degree_default_lpp(int l_max, int dtype, int qprec) {
 // lanes) is fastest; beyond POINT's range FP32 arithmetic runs on ROW up to
 // its l_max 63 (1.8-2.2x SLICE), then on SLICE (DEGREE for bf16 storage);
 // Hessians stay on POINT / SLICE.
-int auto_family(int l_max, int dtype, int out, int qprec, bool hess) {
+int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
     if (!hess && (mixed || (dtype == SPH_F64 && l_max >= 12))) return SPH_KERNEL_DEGREE;
+    if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
     if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
     if (!hess && dtype == SPH_F32 && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && out == SPH_OUT_BF16) return SPH_KERNEL_DEGREE;
@@ -359,7 +421,8 @@ int check_common(int64_t n, int l_max, int dtype, int kernel) {
         return SPH_EINVAL;
     }
     if (kernel != SPH_KERNEL_AUTO && kernel != SPH_KERNEL_POINT && kernel != SPH_KERNEL_SLICE &&
-        kernel != SPH_KERNEL_DEGREE && kernel != SPH_KERNEL_DEGREE_DOWN && kernel != SPH_KERNEL_ROW) {
+        kernel != SPH_KERNEL_DEGREE && kernel != SPH_KERNEL_DEGREE_DOWN && kernel != SPH_KERNEL_ROW &&
+        kernel != SPH_KERNEL_POINT_HC) {
         set_error("kernel=%d is not an sph_kernel", kernel);
         return SPH_EINVAL;
     }
@@ -391,6 +454,7 @@ const char* sphericart_last_error(void) { return last_error_message(); }
 
 int sphericart_max_l(int dtype, int qprec, int kernel) {
     if (kernel == SPH_KERNEL_POINT) return (qprec == SPH_Q_F64 && dtype == SPH_F32) ? -1 : SPH_MAX_L_POINT;
+    if (kernel == SPH_KERNEL_POINT_HC) return (qprec == SPH_Q_F64 && dtype == SPH_F32) ? -1 : kHcMaxL;
     if (kernel == SPH_KERNEL_ROW) return (dtype == SPH_F32 && qprec == SPH_Q_NATIVE) ? kRowMaxL : -1;
     (void)dtype;
     return SPH_MAX_L;
@@ -432,7 +496,17 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     const int grad = dsph ? 1 : 0;
     int fam = kernel;
     const bool hess_bf16 = ddsph && out == SPH_OUT_BF16;
-    if (fam == SPH_KERNEL_AUTO) fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr);
+    if (fam == SPH_KERNEL_AUTO) fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr, dsph != nullptr);
+    int hc = 0;
+    if (fam == SPH_KERNEL_POINT_HC) {
+        if (l_max > kHcMaxL || ddsph || mixed || out != SPH_OUT_SAME) {
+            set_error("POINT_HC takes l_max <= %d, values and gradients, native Q precision and same-type storage",
+                      kHcMaxL);
+            return SPH_EUNSUPPORTED;
+        }
+        hc = 1;
+        fam = SPH_KERNEL_POINT;
+    }
     if (fam == SPH_KERNEL_POINT && (l_max > SPH_MAX_L_POINT || hess_bf16 || mixed)) {
         set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
@@ -464,6 +538,7 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     FwdArgs a{xyz, n, l_max, normalized ? 1 : 0, dtype, out, qprec, sph, dsph, ddsph, stream, sph_launch{0, 0, 0, 0},
               nullptr};
     if (launch) a.launch = *launch;
+    a.hc = hc;
     if (fam == SPH_KERNEL_POINT) {
         bool from_default = !launch;
         if (!launch) {
@@ -566,7 +641,7 @@ static int backward_common(const void* xyz, const void* g, const void* v, int64_
         set_error("POINT kernels take l_max <= %d", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
-    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN) {
+    if (fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN || fam == SPH_KERNEL_POINT_HC) {
         set_error("backward passes run on the POINT, ROW (backward) or SLICE kernels");
         return SPH_EUNSUPPORTED;
     }
@@ -667,7 +742,9 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         return SPH_EINVAL;
     }
     const int eo = elem_size(dtype, out);
-    const int fam = auto_family(l_max, dtype, out, SPH_Q_NATIVE, hess != 0);
+    int fam = auto_family(l_max, dtype, out, SPH_Q_NATIVE, hess != 0, grad != 0);
+    const bool hc = fam == SPH_KERNEL_POINT_HC;
+    if (hc) fam = SPH_KERNEL_POINT;  // same launch shapes
     if (fam == SPH_KERNEL_DEGREE) {
         *kernel_out = SPH_KERNEL_DEGREE;
         *launch_out = sph_launch{0, 0, 0, degree_default_lpp(l_max, dtype, SPH_Q_NATIVE)};
@@ -675,7 +752,7 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         *kernel_out = SPH_KERNEL_ROW;
         *launch_out = sph_launch{0, 1, 0, 8};
     } else if (fam == SPH_KERNEL_POINT) {
-        *kernel_out = SPH_KERNEL_POINT;
+        *kernel_out = hc ? SPH_KERNEL_POINT_HC : SPH_KERNEL_POINT;
         sph_launch s{0, 0, 0, 0};
         int d = -1;
         if (cudaGetDevice(&d) != cudaSuccess) {

@@ -60,6 +60,14 @@ const void* device_tables(int dtype);
 // S = Qtilde_l^l on the diagonal.
 const void* device_tables_down(int dtype);
 
+// Coefficient streams of the ROW kernels, FP32 (see sph_capi.cu): entry
+// (degree, slot, lane), lane fastest, kRowDegrees x kRowSlots x kRowLanes
+// float4 entries, then as many floats.
+constexpr int kRowLanes = 8;
+constexpr int kRowDegrees = 64;
+constexpr int kRowSlots = 8;
+const void* device_row_tables();
+
 // Per-device status word written by kernels whose bounded waits time out.
 uint32_t* device_status_word();
 
@@ -85,7 +93,15 @@ struct FwdArgs {
     void* stream;
     sph_launch launch;   // resolved launch shape
     uint32_t* status;
+    int hc = 0;          // POINT: hard-coded degrees l <= 3, then the recursion (l_max <= kHcMaxL)
 };
+
+// Largest l_max with the hybrid POINT forward (hard-coded l <= 3) compiled.
+constexpr int kHcMaxL = 8;
+
+// Whether AUTO runs the hybrid instead of the all-recursion POINT forward
+// (values, or values and gradients; no Hessians).
+bool point_hybrid_wins(int l_max, int dtype, bool grad);
 
 struct BwdArgs {
     const void* xyz;
@@ -115,6 +131,12 @@ PointBwdFn point_dbwd_fn(int L);
 struct BatchClassArgs;
 using BatchClassFn = int (*)(const BatchClassArgs&);
 BatchClassFn batch_class_fn(int L);
+
+// One-launch ragged-batch kernel from device descriptors, one object file
+// per flag class gn = gradients + 2 * normalized.
+struct OneArgs;
+using BatchOneFn = int (*)(const OneArgs&);
+BatchOneFn batch_one_fn(int gn);
 
 // Tuned POINT forward shape installed for (l_max, dtype, out, grad) on the
 // current device; false if none.

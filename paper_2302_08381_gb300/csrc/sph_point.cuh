@@ -25,6 +25,7 @@
 #include <utility>
 
 #include "sph_core.cuh"
+#include "sph_hardcoded.cuh"
 #include "sph_internal.h"
 
 namespace sph {
@@ -74,27 +75,16 @@ PointTabs<L, T, HESS> make_point_tabs() {
     return t;
 }
 
-// The unrolled recursion for one point. (x, y, z, r2) are the coordinates the
-// polynomials are evaluated at (already divided by r for the normalized form).
-// Calls vis.emit(l, k, Deriv) once per output column k = l*l + l + m.
-template <int L, bool GRAD, bool HESS, typename T, typename Tabs, typename Vis>
-__device__ __forceinline__ void point_core(T x, T y, T z, T r2, const Tabs& tb, Vis& vis) {
-    T c[L + 1], s[L + 1];
-    c[0] = T(1);
-    s[0] = T(0);
+// The unrolled recursion for one point from degree L0 on. (x, y, z, r2) are
+// the coordinates the polynomials are evaluated at (already divided by r for
+// the normalized form); c, s hold c_m, s_m for m <= L; q1, q2 hold
+// Qtilde_{L0-1}^m and Qtilde_{L0-2}^m (zero for m beyond the degree).
+// Calls vis.emit(l, k, Deriv) once per output column k = l*l + l + m, l >= L0.
+template <int L, int L0, bool GRAD, bool HESS, typename T, typename Tabs, typename Vis>
+__device__ __forceinline__ void point_core_from(T x, T y, T z, T r2, const Tabs& tb, Vis& vis, const T (&c)[L + 1],
+                                                const T (&s)[L + 1], T (&q1)[L + 1], T (&q2)[L + 1]) {
 #pragma unroll
-    for (int m = 1; m <= L; ++m) {  // Eq. iter-sc
-        c[m] = x * c[m - 1] - y * s[m - 1];
-        s[m] = x * s[m - 1] + y * c[m - 1];
-    }
-    T q1[L + 1], q2[L + 1];  // Qtilde_{l-1}^m, Qtilde_{l-2}^m
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-        q1[m] = T(0);
-        q2[m] = T(0);
-    }
-#pragma unroll
-    for (int l = 0; l <= L; ++l) {
+    for (int l = L0; l <= L; ++l) {
         T q[L + 1];
         q[l] = tb.qll[l];
         if (l >= 1) q[l - 1] = tb.d[l] * z * q1[l - 1];
@@ -135,6 +125,61 @@ __device__ __forceinline__ void point_core(T x, T y, T z, T r2, const Tabs& tb, 
             q2[m] = q1[m];
             q1[m] = q[m];
         }
+    }
+}
+
+template <int L, typename T>
+__device__ __forceinline__ void point_cs(T x, T y, T (&c)[L + 1], T (&s)[L + 1]) {
+    c[0] = T(1);
+    s[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {  // Eq. iter-sc
+        c[m] = x * c[m - 1] - y * s[m - 1];
+        s[m] = x * s[m - 1] + y * c[m - 1];
+    }
+}
+
+// The whole recursion for one point (every degree from 0).
+template <int L, bool GRAD, bool HESS, typename T, typename Tabs, typename Vis>
+__device__ __forceinline__ void point_core(T x, T y, T z, T r2, const Tabs& tb, Vis& vis) {
+    T c[L + 1], s[L + 1];
+    point_cs<L>(x, y, c, s);
+    T q1[L + 1], q2[L + 1];  // Qtilde_{l-1}^m, Qtilde_{l-2}^m
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        q1[m] = T(0);
+        q2[m] = T(0);
+    }
+    point_core_from<L, 0, GRAD, HESS>(x, y, z, r2, tb, vis, c, s, q1, q2);
+}
+
+// Hybrid (Section 3.2: hard-coded low degrees, the general recursion above):
+// degrees l <= min(L, 3) from the generated straight-line expressions of
+// sph_hardcoded.cuh, which also give Qtilde_LH^m and Qtilde_{LH-1}^m, and
+// Eq. iter-q from degree LH + 1. Values and gradients (no Hessians).
+template <int L, bool GRAD, typename T, typename Tabs, typename Vis>
+__device__ __forceinline__ void point_core_hc(T x, T y, T z, T r2, const Tabs& tb, Vis& vis) {
+    constexpr int LH = L < 3 ? L : 3;
+    T qa[4] = {T(0), T(0), T(0), T(0)}, qb[4] = {T(0), T(0), T(0), T(0)};
+    if constexpr (LH == 0) {
+        if constexpr (GRAD) hardcoded_l0_grad(x, y, z, r2, vis, qa, qb); else hardcoded_l0_val(x, y, z, r2, vis, qa, qb);
+    } else if constexpr (LH == 1) {
+        if constexpr (GRAD) hardcoded_l1_grad(x, y, z, r2, vis, qa, qb); else hardcoded_l1_val(x, y, z, r2, vis, qa, qb);
+    } else if constexpr (LH == 2) {
+        if constexpr (GRAD) hardcoded_l2_grad(x, y, z, r2, vis, qa, qb); else hardcoded_l2_val(x, y, z, r2, vis, qa, qb);
+    } else {
+        if constexpr (GRAD) hardcoded_l3_grad(x, y, z, r2, vis, qa, qb); else hardcoded_l3_val(x, y, z, r2, vis, qa, qb);
+    }
+    if constexpr (L > LH) {
+        T c[L + 1], s[L + 1];
+        point_cs<L>(x, y, c, s);
+        T q1[L + 1], q2[L + 1];
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            q1[m] = m <= LH ? qa[m <= LH ? m : 0] : T(0);
+            q2[m] = m <= LH - 1 ? qb[m <= LH - 1 ? m : 0] : T(0);
+        }
+        point_core_from<L, LH + 1, GRAD, false>(x, y, z, r2, tb, vis, c, s, q1, q2);
     }
 }
 
@@ -208,7 +253,7 @@ __device__ __forceinline__ void warp_rows_in(T* __restrict__ sdst, const T* __re
     }
 }
 
-template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO>
+template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO, bool HC = false>
 __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xyz, int64_t n,
                                                         const __grid_constant__ PointTabs<L, T, HESS> tb,
                                                         TO* __restrict__ sph, TO* __restrict__ dsph,
@@ -262,7 +307,10 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
             }
             FwdVis<T, TO, GRAD, HESS, NORM, K> vis{s_v + size_t(lane) * RS::V, s_d + size_t(lane) * RS::D,
                                                    s_h + size_t(lane) * RS::H, x, y, z, ir};
-            point_core<L, GRAD, HESS>(x, y, z, r2, tb, vis);
+            if constexpr (HC && !HESS)
+                point_core_hc<L, GRAD>(x, y, z, r2, tb, vis);
+            else
+                point_core<L, GRAD, HESS>(x, y, z, r2, tb, vis);
         }
         if constexpr (RS::PAD) {
             __syncwarp();
@@ -587,12 +635,12 @@ inline int grid_for(K kern, int threads, size_t smem, int64_t work_warps, int bl
     return int(std::max<int64_t>(1, std::min(want, cap)));
 }
 
-template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO>
+template <int L, bool GRAD, bool HESS, bool NORM, typename T, typename TO, bool HC = false>
 int launch_point_fwd(const FwdArgs& a) {
     static const PointTabs<L, T, HESS> tb = make_point_tabs<L, T, HESS>();
     const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
     const size_t smem = size_t(W) * point_fwd_warp_bytes<L, GRAD, HESS, TO>(P);
-    auto kern = point_fwd_kernel<L, GRAD, HESS, NORM, T, TO>;
+    auto kern = point_fwd_kernel<L, GRAD, HESS, NORM, T, TO, HC>;
     cudaError_t err = ensure_smem(kern, smem);
     if (err != cudaSuccess) return int(err);
     const int64_t ntiles = ceil_div(a.n, P);

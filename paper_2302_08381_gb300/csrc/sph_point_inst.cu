@@ -28,6 +28,21 @@ int SPH_CAT(point_fwd_L, SPH_INST_L)(const FwdArgs& a) {
         return norm ? launch_point_fwd<L, true, true, true, float, float>(a)
                     : launch_point_fwd<L, true, true, false, float, float>(a);
     }
+    if (a.hc) {  // hybrid: hard-coded l <= 3, the recursion above (values and gradients)
+        if constexpr (L <= kHcMaxL) {
+#define SPH_FWD_HC(T, TO)                                                            \
+    return grad ? (norm ? launch_point_fwd<L, true, false, true, T, TO, true>(a)      \
+                        : launch_point_fwd<L, true, false, false, T, TO, true>(a))    \
+                : (norm ? launch_point_fwd<L, false, false, true, T, TO, true>(a)     \
+                        : launch_point_fwd<L, false, false, false, T, TO, true>(a));
+            if (a.dtype == SPH_F64) {
+                SPH_FWD_HC(double, double)
+            }
+            SPH_FWD_HC(float, float)
+#undef SPH_FWD_HC
+        }
+        return int(cudaErrorInvalidValue);
+    }
     if (a.dtype == SPH_F64) {
         SPH_FWD(double, double)
     }

@@ -36,6 +36,13 @@ static const BatchClassFn kBatch[] = {SPH_ROW(0),  SPH_ROW(1),  SPH_ROW(2),  SPH
                                       SPH_ROW(12), SPH_ROW(13), SPH_ROW(14), SPH_ROW(15), SPH_ROW(16)};
 #undef SPH_ROW
 
+int batch_one_gn0(const OneArgs&);
+int batch_one_gn1(const OneArgs&);
+int batch_one_gn2(const OneArgs&);
+int batch_one_gn3(const OneArgs&);
+static const BatchOneFn kOne[] = {batch_one_gn0, batch_one_gn1, batch_one_gn2, batch_one_gn3};
+BatchOneFn batch_one_fn(int gn) { return (gn >= 0 && gn <= 3) ? kOne[gn] : nullptr; }
+
 BatchClassFn batch_class_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kBatch[L] : nullptr; }
 PointFwdFn point_fwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kFwd[L] : nullptr; }
 PointBwdFn point_bwd_fn(int L) { return (L >= 0 && L <= SPH_MAX_L_POINT) ? kBwd[L] : nullptr; }

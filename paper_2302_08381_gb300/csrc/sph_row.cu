@@ -69,25 +69,35 @@ struct CSf {
     }
 };
 
+// Forward kernel. Per degree d and channel slot k (m = j + 8k) a lane runs
+// one step of Eq. iter-q (coefficients from the lane-interleaved table, one
+// degree ahead, so no index arithmetic), then Eq. real-sh-cartesian and
+// Eq. iter-deri for the columns d^2+d+m and d^2+d-m of every plane, stored
+// through per-window plane pointers at compile-time offsets. The m = 0
+// column takes the same path with c_0 = 1/sqrt2 and s_0 = 0 (its -m stores
+// land on the same column first and are overwritten).
 template <typename TO, bool GRAD, bool NORM, int NCH>
 __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ xyz, int64_t n, int L,
-                                                      const float* __restrict__ tb, float inv_sqrt2,
+                                                      const float4* __restrict__ rowA,
+                                                      const float* __restrict__ rowF, float inv_sqrt2,
                                                       TO* __restrict__ sph, TO* __restrict__ dsph) {
     constexpr int NPL = GRAD ? 4 : 1;
     constexpr int SE = RowGeom<TO>::SE;
     constexpr int BUF = RowGeom<TO>::BUF;
+    constexpr int PSTR = RowGeom<TO>::template point_stride<NPL>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
     const int g = lane / kG;  // point of the warp tile
     const int j = lane % kG;  // channel class m = j (mod 8)
-    constexpr int PSTR = RowGeom<TO>::template point_stride<NPL>();
     TO* const pst = reinterpret_cast<TO*>(smem) + (size_t(warp) * kPW + g) * PSTR;  // this point's planes
     const int64_t K = int64_t(L + 1) * (L + 1);
     const int64_t ntiles = (n + kPW - 1) / kPW;
-    const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tb);
     const int nb_lane = (lane & ~(kG - 1)) | ((j + 1) & (kG - 1));  // the lane holding channel m+1's class
+    // this lane's stream: entry (d, k) at laneA[(d * kRowSlots + k) * kRowLanes]
+    const float4* const laneA = rowA + j;
+    const float* const laneF = rowF + j;
 
     for (int64_t tile = int64_t(blockIdx.x) * W + warp; tile < ntiles; tile += int64_t(gridDim.x) * W) {
         const int64_t p = tile * kPW + g;
@@ -107,7 +117,8 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
         }
         const float r2 = fmaf(z, z, fmaf(x, x, y * y));
 
-        // c_m + i s_m and c_{m-1} + i s_{m-1} of the lane's channels m = j + 8k.
+        // c_m + i s_m and c_{m-1} + i s_{m-1} of the lane's channels m = j + 8k
+        // (Eq. iter-sc); c_0 carries the 1/sqrt2 of the m = 0 column.
         float cm[NCH], sm[NCH], cm1[NCH], sm1[NCH];
         {
             const CSf xy{x, y};
@@ -122,9 +133,9 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
             if (j == 0) b = p7;  // channel 8k (k >= 1) needs (x + i y)^(8k-1)
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
-                cm[k] = a.c;
-                sm[k] = a.s;
-                const bool none = (j == 0 && k == 0);  // m = 0 has no c_{m-1}
+                const bool none = (j == 0 && k == 0);  // m = 0: no c_{m-1}
+                cm[k] = none ? inv_sqrt2 : a.c;
+                sm[k] = none ? 0.f : a.s;
                 cm1[k] = none ? 0.f : b.c;
                 sm1[k] = none ? 0.f : b.s;
                 a = a.times(w8);
@@ -148,21 +159,14 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
             s[i] = (SE - phase) % SE;
         }
 
-        // Coefficients of degree d for the lane's channels (clamped to a valid
-        // entry where m > d), loaded one degree ahead.
+        // Degree-0 coefficients; later degrees are loaded one degree ahead.
         float4 ta[NCH];
         float tf[NCH];
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
-            const int i = tri(0, 0);
-            ta[k] = t4[2 * i];
-            tf[k] = tb[8 * i + 4];
+            ta[k] = laneA[k * kRowLanes];
+            tf[k] = laneF[k * kRowLanes];
         }
-
-        // Per-point factors of the chain rule of the normalized form (Section 3:
-        // dY/dx_i = (1/r)[dYt/dx_i(u) - l u_i Yt(u)]): the 1/r is folded into
-        // the multipliers of the derivative terms, the l u_i / r into the
-        // per-degree constants (ax, ay, az) below.
         const float xi = NORM ? x * ir : x, yi = NORM ? y * ir : y;
         const float jf = float(j);
 
@@ -172,25 +176,27 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
             // A window of whole degrees [l, lw): columns [l^2, lw^2).
             int lw = l + 1;
             while (lw <= L && (lw + 1) * (lw + 1) - l * l <= kCap - (SE - 1)) ++lw;
-            // Stage element of column c in plane i: pst[ob[i] + c].
-            int ob[NPL];
+            // Column c of plane i is staged at pst[i * BUF + SE - s[i] + c].
+            TO* pp[NPL];  // + j: the +m columns
+            TO* pn[NPL];  // - j: the -m columns
 #pragma unroll
-            for (int i = 0; i < NPL; ++i) ob[i] = i * BUF + SE - s[i];
+            for (int i = 0; i < NPL; ++i) {
+                pp[i] = pst + (i * BUF + SE - s[i] + j);
+                pn[i] = pst + (i * BUF + SE - s[i] - j);
+            }
             for (int d = l; d < lw; ++d) {
                 const int ctr = d * d + d;
                 const int kend = d / kG;  // channels m = j + 8k <= d need k <= d/8 (same for the whole warp)
-                const int dn = d < L ? d + 1 : L;
-                // all NCH slots are loaded and copied every degree: with a
-                // degree-dependent bound here the compiler keeps more live
-                // registers and the kernel ran ~10 % slower at l_max >= 30
+                const int kn = (d + 1) / kG;
+                const int dn = d < L ? d + 1 : d;
+                // all slots every degree (zeros where m > d): a degree-dependent
+                // bound here keeps more registers live and ran slower
                 float4 na[NCH];
                 float nf[NCH];
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {  // coefficients of the next degree
-                    const int mk = j + kG * k;
-                    const int i = tri(dn, mk <= dn ? mk : dn);
-                    na[k] = t4[2 * i];
-                    if (GRAD) nf[k] = tb[8 * i + 4];
+                    na[k] = laneA[(dn * kRowSlots + k) * kRowLanes];
+                    if (GRAD) nf[k] = laneF[(dn * kRowSlots + k) * kRowLanes];
                 }
                 float ax = 0.f, ay = 0.f, az = 0.f;
                 if (NORM && GRAD) {
@@ -199,50 +205,43 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
                     ay = lir * y;
                     az = lir * z;
                 }
+                TO* qp[NPL];
+                TO* qn_[NPL];
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    qp[i] = pp[i] + ctr;
+                    qn_[i] = pn[i] + ctr;
+                }
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     if (k > kend) break;
-                    const int m = j + kG * k;
-                    const bool on = m <= d;
                     const float4 t0 = ta[k];  // {A, B, S, e}
                     const float src = (j == 0) ? (k + 1 < NCH ? q1[k + 1 < NCH ? k + 1 : k] : 0.f) : q1[k];
-                    const float qn = __shfl_sync(0xffffffffu, src, nb_lane);  // Qtilde_{l-1}^{m+1}
-                    float q = fmaf(t0.x * z, q1[k], fmaf(-(t0.y * r2), q2[k], t0.z));
-                    q = on ? q : 0.f;
-                    if (on) {
-                        // Eq. real-sh-cartesian and Eq. iter-deri (prefactors folded).
-                        const float E1 = t0.w * qn;                       // e Qtilde_{l-1}^{m+1}
-                        const float Qz = NORM ? (tf[k] * q1[k]) * ir : tf[k] * q1[k];
-                        const float Qx = xi * E1, Qy = yi * E1;
-                        if (k == 0 && j == 0) {                           // m = 0
-                            const float v = q * inv_sqrt2;
-                            pst[ob[0] + ctr] = OutConv<TO>::cv(v);
-                            if (GRAD) {
-                                pst[ob[1 % NPL] + ctr] = OutConv<TO>::cv(NORM ? fmaf(-ax, v, Qx) : Qx);
-                                pst[ob[2 % NPL] + ctr] = OutConv<TO>::cv(NORM ? fmaf(-ay, v, Qy) : Qy);
-                                pst[ob[3 % NPL] + ctr] = OutConv<TO>::cv(NORM ? fmaf(-az, v, Qz) : Qz);
-                            }
-                        } else {
-                            const float c = cm[k], sn = sm[k], c1 = cm1[k], s1 = sm1[k];
-                            const float vc = q * c, vs = q * sn;          // +m (cos) and -m (sin) columns
-                            const int cp = ctr + m, cn = ctr - m;
-                            pst[ob[0] + cp] = OutConv<TO>::cv(vc);
-                            pst[ob[0] + cn] = OutConv<TO>::cv(vs);
-                            if (GRAD) {
-                                const float mQ = (NORM ? (jf + float(kG * k)) * ir : jf + float(kG * k)) * q;
-                                const float mc1 = mQ * c1, ms1 = mQ * s1;
-                                // scaled: -a * v terms vanish (a = 0), so they are left out
-                                const float tx_c = NORM ? fmaf(-ax, vc, mc1) : mc1;
-                                const float tx_s = NORM ? fmaf(-ax, vs, ms1) : ms1;
-                                const float ty_c = NORM ? fmaf(-ay, vc, -ms1) : -ms1;
-                                const float ty_s = NORM ? fmaf(-ay, vs, mc1) : mc1;
-                                pst[ob[1 % NPL] + cp] = OutConv<TO>::cv(fmaf(Qx, c, tx_c));
-                                pst[ob[1 % NPL] + cn] = OutConv<TO>::cv(fmaf(Qx, sn, tx_s));
-                                pst[ob[2 % NPL] + cp] = OutConv<TO>::cv(fmaf(Qy, c, ty_c));
-                                pst[ob[2 % NPL] + cn] = OutConv<TO>::cv(fmaf(Qy, sn, ty_s));
-                                pst[ob[3 % NPL] + cp] = OutConv<TO>::cv(NORM ? fmaf(Qz, c, -az * vc) : Qz * c);
-                                pst[ob[3 % NPL] + cn] = OutConv<TO>::cv(NORM ? fmaf(Qz, sn, -az * vs) : Qz * sn);
-                            }
+                    const float qnb = __shfl_sync(0xffffffffu, src, nb_lane);  // Qtilde_{l-1}^{m+1}
+                    // zero for m > d: the table holds zeros there
+                    const float q = fmaf(t0.x * z, q1[k], fmaf(-(t0.y * r2), q2[k], t0.z));
+                    if (j + kG * k <= d) {
+                        const float c = cm[k], sn = sm[k];
+                        const float vc = q * c, vs = q * sn;  // +m (cos) and -m (sin) columns
+                        qn_[0][-kG * k] = OutConv<TO>::cv(vs);
+                        qp[0][kG * k] = OutConv<TO>::cv(vc);
+                        if (GRAD) {
+                            // Eq. iter-deri (prefactors folded)
+                            const float E1 = t0.w * qnb;  // e Qtilde_{l-1}^{m+1}
+                            const float Qz = NORM ? (tf[k] * q1[k]) * ir : tf[k] * q1[k];
+                            const float Qx = xi * E1, Qy = yi * E1;
+                            const float mQ = (NORM ? (jf + float(kG * k)) * ir : jf + float(kG * k)) * q;
+                            const float mc1 = mQ * cm1[k], ms1 = mQ * sm1[k];
+                            const float tx_c = NORM ? fmaf(-ax, vc, mc1) : mc1;
+                            const float tx_s = NORM ? fmaf(-ax, vs, ms1) : ms1;
+                            const float ty_c = NORM ? fmaf(-ay, vc, -ms1) : -ms1;
+                            const float ty_s = NORM ? fmaf(-ay, vs, mc1) : mc1;
+                            qn_[1 % NPL][-kG * k] = OutConv<TO>::cv(fmaf(Qx, sn, tx_s));
+                            qn_[2 % NPL][-kG * k] = OutConv<TO>::cv(fmaf(Qy, sn, ty_s));
+                            qn_[3 % NPL][-kG * k] = OutConv<TO>::cv(NORM ? fmaf(Qz, sn, -az * vs) : Qz * sn);
+                            qp[1 % NPL][kG * k] = OutConv<TO>::cv(fmaf(Qx, c, tx_c));
+                            qp[2 % NPL][kG * k] = OutConv<TO>::cv(fmaf(Qy, c, ty_c));
+                            qp[3 % NPL][kG * k] = OutConv<TO>::cv(NORM ? fmaf(Qz, c, -az * vc) : Qz * c);
                         }
                     }
                     q2[k] = q1[k];
@@ -279,8 +278,10 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
                 }
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
-                    for (int c = j; first && c < s[i]; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
-                    for (int c = e[i] + j; last && c < c_hi; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
+                    if (first)
+                        for (int c = j; c < s[i]; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
+                    if (last)
+                        for (int c = e[i] + j; c < c_hi; c += kG) grow[i][c] = pst[i * BUF + c - s[i] + SE];
                 }
                 if (j == 0) bulk_wait_read_all();  // the buffers are reused below
             }
@@ -546,7 +547,9 @@ __global__ void __launch_bounds__(256) row_bwd_kernel(const float* __restrict__ 
 }
 
 template <typename TO, bool GRAD, bool NORM, int NCH>
-int launch_row(const FwdArgs& a, const float* tb) {
+int launch_row(const FwdArgs& a) {
+    const float* rt = static_cast<const float*>(device_row_tables());
+    if (!rt) return int(cudaErrorMemoryAllocation);
     auto kern = row_fwd_kernel<TO, GRAD, NORM, NCH>;
     const size_t per_warp = row_warp_bytes<TO, GRAD>();
     const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : 1;  // measured: 1 >= 2 > 4 > 8
@@ -570,9 +573,10 @@ int launch_row(const FwdArgs& a, const float* tb) {
     const int64_t ntiles = (a.n + kPW - 1) / kPW;
     const int64_t want = (ntiles + W - 1) / W;
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(bps) * sm_count())));
+    constexpr int kEntries = kRowLanes * kRowDegrees * kRowSlots;
     kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
-        static_cast<const float*>(a.xyz), a.n, a.l_max, tb, float(host_tables().inv_sqrt2), static_cast<TO*>(a.sph),
-        static_cast<TO*>(a.dsph));
+        static_cast<const float*>(a.xyz), a.n, a.l_max, reinterpret_cast<const float4*>(rt), rt + 4 * kEntries,
+        float(host_tables().inv_sqrt2), static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph));
     return int(cudaGetLastError());
 }
 
@@ -613,16 +617,16 @@ int launch_row_bwd_flags(const BwdArgs& a, const float* tb) {
 }
 
 template <typename TO, int NCH>
-int launch_row_flags(const FwdArgs& a, const float* tb) {
+int launch_row_flags(const FwdArgs& a) {
     const bool grad = a.dsph != nullptr, norm = a.normalized != 0;
-    if (grad) return norm ? launch_row<TO, true, true, NCH>(a, tb) : launch_row<TO, true, false, NCH>(a, tb);
-    return norm ? launch_row<TO, false, true, NCH>(a, tb) : launch_row<TO, false, false, NCH>(a, tb);
+    if (grad) return norm ? launch_row<TO, true, true, NCH>(a) : launch_row<TO, true, false, NCH>(a);
+    return norm ? launch_row<TO, false, true, NCH>(a) : launch_row<TO, false, false, NCH>(a);
 }
 
 template <int NCH>
-int launch_row_out(const FwdArgs& a, const float* tb) {
-    if (a.out == SPH_OUT_BF16) return launch_row_flags<__nv_bfloat16, NCH>(a, tb);
-    return launch_row_flags<float, NCH>(a, tb);
+int launch_row_out(const FwdArgs& a) {
+    if (a.out == SPH_OUT_BF16) return launch_row_flags<__nv_bfloat16, NCH>(a);
+    return launch_row_flags<float, NCH>(a);
 }
 
 }  // namespace
@@ -642,15 +646,13 @@ int row_bwd_part0(const BwdArgs& a) {
 }
 
 int row_fwd_part0(const FwdArgs& a) {
-    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
-    if (!tb) return int(cudaErrorMemoryAllocation);
     switch ((a.l_max + 1 + kG - 1) / kG) {
         case 3:
-            return launch_row_out<3>(a, tb);
+            return launch_row_out<3>(a);
         case 4:
-            return launch_row_out<4>(a, tb);
+            return launch_row_out<4>(a);
         default:
-            return launch_row_out<5>(a, tb);
+            return launch_row_out<5>(a);
     }
 }
 #else
@@ -668,15 +670,13 @@ int row_bwd_part1(const BwdArgs& a) {
 }
 
 int row_fwd_part1(const FwdArgs& a) {
-    const float* tb = static_cast<const float*>(device_tables(SPH_F32));
-    if (!tb) return int(cudaErrorMemoryAllocation);
     switch ((a.l_max + 1 + kG - 1) / kG) {
         case 6:
-            return launch_row_out<6>(a, tb);
+            return launch_row_out<6>(a);
         case 7:
-            return launch_row_out<7>(a, tb);
+            return launch_row_out<7>(a);
         default:
-            return launch_row_out<8>(a, tb);
+            return launch_row_out<8>(a);
     }
 }
 #endif

@@ -153,6 +153,8 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, i
     const int Ps[] = {32, 28, 24, 20, 16, 12, 8, 4, 2, 1};
     const int Ws[] = {1, 2, 4, 8};
     const int Bs[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};  // > occupancy: blocks scheduled in waves
+    // the POINT variant AUTO runs for this request (both take the same shapes)
+    const int fam = point_hybrid_wins(l_max, dtype, grad != 0) ? SPH_KERNEL_POINT_HC : SPH_KERNEL_POINT;
     for (int P : Ps) {
         if (P % mult != 0) continue;
         for (int W : Ws) {
@@ -160,8 +162,8 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, i
             if (smem > size_t(max_smem_optin())) continue;
             for (int B : Bs) {
                 sph_launch s{P, W, B, 0};
-                int stt = sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE,
-                                                SPH_KERNEL_POINT, &s, sph, dsph, nullptr, stream);
+                int stt = sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE, fam, &s, sph,
+                                                dsph, nullptr, stream);
                 if (stt != SPH_OK) {
                     cudaGetLastError();
                     continue;  // shape not launchable here (occupancy, limits)
@@ -169,8 +171,8 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, i
                 std::vector<float> ts;
                 for (int r = 0; r < reps; ++r) {
                     cudaEventRecord(ev.a, st);
-                    sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE, SPH_KERNEL_POINT, &s,
-                                          sph, dsph, nullptr, stream);
+                    sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE, fam, &s, sph, dsph,
+                                          nullptr, stream);
                     cudaEventRecord(ev.b, st);
                     if (cudaEventSynchronize(ev.b) != cudaSuccess) {
                         set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));

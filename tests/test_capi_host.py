@@ -190,7 +190,13 @@ def test_argument_errors_before_any_cuda_call():
     for k in (C.SPH_KERNEL_DEGREE, C.SPH_KERNEL_DEGREE_DOWN):
         assert _err(C.sphericart_compute_ex, 16, 4, 30, 0, 0, 0, 0, k, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
         assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, k, launch, 16, none) == C.SPH_EUNSUPPORTED
-    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 6, launch, 16, none, none, none) == C.SPH_EINVAL
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 7, launch, 16, none, none, none) == C.SPH_EINVAL
+    # POINT_HC (hard-coded l <= 3 + recursion): l_max <= 8, no Hessians, no bf16 storage
+    hc = C.SPH_KERNEL_POINT_HC
+    assert _err(C.sphericart_compute_ex, 16, 4, 9, 0, 0, 0, 0, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 1, 0, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, hc, launch, 16, 32, 32, none) == C.SPH_EUNSUPPORTED
+    assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 1, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
     # ROW: FP32 arithmetic, 16 <= l_max <= 63, no Hessians; backward (FP32) but no double backward
     R = C.SPH_KERNEL_ROW
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
@@ -273,8 +279,13 @@ def test_point_default_shapes():
     up to 32 points within 74 KB with one warp per block."""
     fam, s = C.sphericart_launch_info(8, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
     assert fam == C.SPH_KERNEL_POINT and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (32, 4, 16)
+    # FP64 with gradients up to l_max 8 runs the hybrid (hard-coded l <= 3) on the same shapes
     fam, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
-    assert fam == C.SPH_KERNEL_POINT and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (28, 1, 16)
+    assert fam == C.SPH_KERNEL_POINT_HC and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (28, 1, 16)
+    assert C.sphericart_launch_info(3, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT_HC
+    assert C.sphericart_launch_info(4, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT
+    assert C.sphericart_launch_info(9, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_POINT
+    assert C.sphericart_launch_info(3, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_POINT
     assert 28 * 4 * 81 * 8 <= 74 * 1024 < 30 * 4 * 81 * 8  # the largest even tile inside 74 KB
     _, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)
     assert (s.points_per_tile, s.warps_per_block) == (32, 1)
