@@ -362,8 +362,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / backward / oracle legs")
     ap.add_argument(
         "--profile",
-        choices=["fwd", "fwd64", "bwd", "dbwd", "batch", "expansion", "slice20", "degree20", "row20", "hess",
-                 "degree50_f64"],
+        choices=["fwd", "fwd64", "bwd", "dbwd", "batch", "batched", "expansion", "slice20", "degree20", "row20",
+                 "hess", "degree50_f64"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
     ap.add_argument("--dry-run", action="store_true",
@@ -577,7 +577,7 @@ def run_profile(args):
         _build.build()
     dev = torch.device("cuda", 0)
     n = args.n
-    if args.profile in ("fwd", "fwd64", "batch", "hess"):
+    if args.profile in ("fwd", "fwd64", "batch", "batched", "hess"):
         L = L_MAX
     elif args.profile in ("slice20", "degree20", "row20"):
         L = 20
@@ -628,8 +628,15 @@ def run_profile(args):
         sizes = np.maximum(1, (sizes * scale).astype(np.int64))
         offs = np.concatenate([[0], np.cumsum(sizes)])
         xt = torch.from_numpy(xyz[: offs[-1]]).to(dev)
-        plan = api.BatchPlan([xt[offs[i]:offs[i + 1]] for i in range(len(sizes))], [int(v) for v in lmax])
-        fn = plan.execute
+        xs = [xt[offs[i]:offs[i + 1]] for i in range(len(sizes))]
+        ls = [int(v) for v in lmax]
+        if args.profile == "batch":  # the plan: one launch per l_max class
+            plan = api.BatchPlan(xs, ls)
+            fn = plan.execute
+        else:  # sphericart_compute_batched: one launch
+            outs = [(torch.empty((x.shape[0], (L + 1) ** 2), device=dev),
+                     torch.empty((x.shape[0], 3, (L + 1) ** 2), device=dev)) for x, L in zip(xs, ls)]
+            fn = lambda: api.compute_batched(xs, ls, outputs=outs)  # noqa: E731
     for _ in range(args.warmup + args.steps):
         fn()
     torch.cuda.synchronize()

@@ -129,7 +129,7 @@ typedef enum {
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
  * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
- * (0..8, 0 = 1) and blocks_per_sm.
+ * (forward 0..2, backward 0..8; 0 = 1 forward, 2 backward) and blocks_per_sm.
  * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
  * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
  * the FP64 pipe); when a call has fewer than 2 x SMs x warps_per_block tiles,
@@ -359,6 +359,32 @@ int sphericart_compute_batched_ex(const sph_batch_set* desc, int nsets, int flag
  * caller's, as everywhere. */
 int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int nsets,
                                      const sph_launch* launch, void* stream);
+
+/* ------------------------------------------------------------ e3nn convention
+ * Normalizations of sphericart_compute_e3nn (e3nn's names). */
+typedef enum {
+    SPH_E3NN_INTEGRAL = 0,   /* each component squared integrates to 1 over the sphere */
+    SPH_E3NN_COMPONENT = 1,  /* sum_m Y_l^m(u)^2 = 2l + 1 on the unit sphere */
+    SPH_E3NN_NORM = 2        /* sum_m Y_l^m(u)^2 = 1 on the unit sphere */
+} sph_e3nn_norm;
+
+/* sphericart_compute_e3nn: the harmonics in e3nn's convention (Section 3.2:
+ * the paper's library provides wrappers with e3nn's conventions), so that
+ * models written against e3nn can switch. e3nn's polar axis is y: its output
+ * equals this library's at the permuted point (z, x, y), times sqrt(4 pi)
+ * (component) or sqrt(4 pi / (2l+1)) (norm) per l block, with the gradient
+ * planes in (d/dx, d/dy, d/dz) order.
+ *   xyz        [n,3] device, dtype (SPH_F32 or SPH_F64)
+ *   normalize  1 = inputs normalized to the unit sphere (e3nn's normalize=True),
+ *              0 = polynomial (scaled) form
+ *   workspace  device [n,3] of the dtype (the permuted points), caller-owned
+ *   sph        [n,(l_max+1)^2]; dsph [n,3,(l_max+1)^2] or NULL
+ * Two small kernels surround the forward: the permutation, and (unless the
+ * normalization is "integral" without gradients) an in-place rescale and
+ * plane reorder, which reads and writes the outputs once more. Errors as
+ * sphericart_compute_ex, SPH_EINVAL for a bad normalization or NULL workspace. */
+int sphericart_compute_e3nn(const void* xyz, int64_t n, int l_max, int normalize, int normalization,
+                            int dtype, void* workspace, void* sph, void* dsph, void* stream);
 
 /* ----------------------------------------------------------------- services
  * sphericart_last_error: message of the last failed call on this thread

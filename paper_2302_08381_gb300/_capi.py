@@ -22,6 +22,7 @@ SPH_KERNEL_AUTO, SPH_KERNEL_POINT, SPH_KERNEL_SLICE, SPH_KERNEL_DEGREE, SPH_KERN
 SPH_KERNEL_POINT_HC = 6
 SPH_BATCH_PER_LMAX, SPH_BATCH_ONE_LAUNCH = 0, 1
 SPH_BATCHED_GRADIENTS, SPH_BATCHED_NORMALIZED = 1, 2
+SPH_E3NN_INTEGRAL, SPH_E3NN_COMPONENT, SPH_E3NN_NORM = 0, 1, 2
 SPH_MAX_L = 128
 SPH_MAX_L_POINT = 16
 
@@ -83,6 +84,7 @@ _PROTOS = {
     "sphericart_batch_plan_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "sphericart_batch_compute_noalloc": (_I, [ctypes.POINTER(sph_batch_set), _I, ctypes.POINTER(sph_launch), _P]),
     "sphericart_compute_batched": (_I, [_P, _I, _I, _P]),
+    "sphericart_compute_e3nn": (_I, [_P, _I64, _I, _I, _I, _I, _P, _P, _P, _P]),
     "sphericart_compute_batched_ex": (_I, [_P, _I, _I, ctypes.POINTER(sph_launch), _P]),
     "sphericart_last_error": (ctypes.c_char_p, []),
     "sphericart_max_l": (_I, [_I, _I, _I]),

@@ -277,6 +277,27 @@ def device_status() -> int:
     return C.sphericart_device_status()
 
 
+_E3NN_NORMS = {"integral": C.SPH_E3NN_INTEGRAL, "component": C.SPH_E3NN_COMPONENT, "norm": C.SPH_E3NN_NORM}
+
+
+def e3nn_spherical_harmonics(xyz, l_max, normalize=False, normalization="integral", gradients=False):
+    """The harmonics in e3nn's convention (``sphericart_compute_e3nn``): y is
+    the polar axis, l = 1 is proportional to (x, y, z), and ``normalization``
+    is "integral", "component" or "norm" as in e3nn. Returns sph [n, K] and,
+    with ``gradients``, dsph [n, 3, K] (d/dx, d/dy, d/dz)."""
+    _check_points(xyz)
+    if normalization not in _E3NN_NORMS:
+        raise ValueError("normalization must be 'integral', 'component' or 'norm'")
+    n, K = xyz.shape[0], n_columns(l_max)
+    ws = torch.empty_like(xyz)
+    sph = torch.empty((n, K), dtype=xyz.dtype, device=xyz.device)
+    dsph = torch.empty((n, 3, K), dtype=xyz.dtype, device=xyz.device) if gradients else None
+    C.check("sphericart_compute_e3nn", C.lib().sphericart_compute_e3nn(
+        xyz.data_ptr(), n, int(l_max), 1 if normalize else 0, _E3NN_NORMS[normalization], _dtype_code(xyz),
+        ws.data_ptr(), sph.data_ptr(), dsph.data_ptr() if dsph is not None else None, _stream(xyz.device)))
+    return (sph, dsph) if gradients else sph
+
+
 def batch_descriptors(xyz_list, lmax_list, sph_list, dsph_list, normalized=False, device=None):
     """sph_batch_set descriptors of point sets as a CUDA uint8 tensor [nsets, 40]
     (the device array ``sphericart_compute_batched`` reads)."""

@@ -604,9 +604,13 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             set_error("ROW launch: warps_per_block must be in [0,8] and blocks_per_sm in [0,32]");
             return SPH_EINVAL;
         }
+        if (a.launch.lanes_per_point < 0 || a.launch.lanes_per_point > 2) {
+            set_error("ROW launch: lanes_per_point selects the window policy: 0 (by l_max), 1 or 2");
+            return SPH_EINVAL;
+        }
         const int e = (l_max + 1 + 7) / 8 <= 5 ? row_fwd_part0(a) : row_fwd_part1(a);
         if (e == int(cudaErrorInvalidConfiguration)) {
-            set_error("ROW launch shape needs more shared memory per block than the device allows");
+            set_error("ROW forward launch shape: at most 2 warps per block, within the device's shared memory");
             return SPH_EINVAL;
         }
         return cuda_status(e, "ROW forward launch");

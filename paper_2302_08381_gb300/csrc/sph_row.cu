@@ -38,17 +38,20 @@ namespace {
 
 constexpr int kG = 8;         // lanes per point
 constexpr int kPW = 32 / kG;  // points per warp
-constexpr int kCap = 256;     // columns a plane buffer holds after its pre-slots
+constexpr int kCap = 256;     // columns buffered before a window is sent (the backward's window size)
 
-// Per output type: elements per 32-byte sector, the plane buffer length (SE
-// pre-slots for the row head, then kCap columns; a multiple of 16 bytes), and
-// the distance between the buffers of consecutive points, which is 8 four-byte
-// words past a multiple of 32 so that the four point groups of a warp, each
-// writing 8 consecutive columns, start 8 banks apart.
-template <typename TO>
+// Per output type, channel slots and window policy: elements per 32-byte
+// sector, the plane buffer length (SE pre-slots for the row head, then kCap
+// columns, or with MINRUN kCap - 1 columns plus one whole degree of at most
+// 16 NCH - 1 columns plus a carried partial sector; a multiple of 16 bytes),
+// and the distance between the buffers of consecutive points, which is 8
+// four-byte words past a multiple of 32 so that the four point groups of a
+// warp, each writing 8 consecutive columns, start 8 banks apart.
+template <typename TO, int NCH, bool MINRUN>
 struct RowGeom {
     static constexpr int SE = 32 / int(sizeof(TO));
-    static constexpr int BUF = SE + kCap;
+    static constexpr int EL16 = 16 / int(sizeof(TO));
+    static constexpr int BUF = MINRUN ? (SE + kCap + 16 * NCH + 8 + EL16 - 1) / EL16 * EL16 : SE + kCap;
     template <int NPL>
     __host__ __device__ static constexpr int point_stride() {
         constexpr int words = NPL * BUF * int(sizeof(TO)) / 4;
@@ -57,9 +60,9 @@ struct RowGeom {
     }
 };
 
-template <typename TO, bool GRAD>
+template <typename TO, bool GRAD, int NCH, bool MINRUN>
 __host__ __device__ constexpr size_t row_warp_bytes() {
-    return size_t(kPW) * RowGeom<TO>::template point_stride<GRAD ? 4 : 1>() * sizeof(TO);
+    return size_t(kPW) * RowGeom<TO, NCH, MINRUN>::template point_stride<GRAD ? 4 : 1>() * sizeof(TO);
 }
 
 struct CSf {
@@ -76,15 +79,17 @@ struct CSf {
 // through per-window plane pointers at compile-time offsets. The m = 0
 // column takes the same path with c_0 = 1/sqrt2 and s_0 = 0 (its -m stores
 // land on the same column first and are overwritten).
-template <typename TO, bool GRAD, bool NORM, int NCH>
-__global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ xyz, int64_t n, int L,
+constexpr int kRowMaxWarps = 2;  // warps per block (measured: 1 >= 2 > 4 > 8); the bound frees registers
+
+template <typename TO, bool GRAD, bool NORM, int NCH, bool MINRUN>
+__global__ void __launch_bounds__(32 * kRowMaxWarps) row_fwd_kernel(const float* __restrict__ xyz, int64_t n, int L,
                                                       const float4* __restrict__ rowA,
                                                       const float* __restrict__ rowF, float inv_sqrt2,
                                                       TO* __restrict__ sph, TO* __restrict__ dsph) {
     constexpr int NPL = GRAD ? 4 : 1;
-    constexpr int SE = RowGeom<TO>::SE;
-    constexpr int BUF = RowGeom<TO>::BUF;
-    constexpr int PSTR = RowGeom<TO>::template point_stride<NPL>();
+    constexpr int SE = RowGeom<TO, NCH, MINRUN>::SE;
+    constexpr int BUF = RowGeom<TO, NCH, MINRUN>::BUF;
+    constexpr int PSTR = RowGeom<TO, NCH, MINRUN>::template point_stride<NPL>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -173,9 +178,11 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
         int l = 0;
         bool first = true;
         while (l <= L) {
-            // A window of whole degrees [l, lw): columns [l^2, lw^2).
-            int lw = l + 1;
-            while (lw <= L && (lw + 1) * (lw + 1) - l * l <= kCap - (SE - 1)) ++lw;
+            // A window of whole degrees [l, lw), the same for every point of
+            // the warp (the lanes shuffle across point groups): degrees are
+            // added while the window fits kCap - SE + 1 new columns, or, with
+            // MINRUN, until it holds at least that many (runs of >= kCap - SE
+            // columns whatever the degree's width, in larger buffers).
             // Column c of plane i is staged at pst[i * BUF + SE - s[i] + c].
             TO* pp[NPL];  // + j: the +m columns
             TO* pn[NPL];  // - j: the -m columns
@@ -184,10 +191,10 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
                 pp[i] = pst + (i * BUF + SE - s[i] + j);
                 pn[i] = pst + (i * BUF + SE - s[i] - j);
             }
-            for (int d = l; d < lw; ++d) {
+            int d = l;
+            while (true) {
                 const int ctr = d * d + d;
                 const int kend = d / kG;  // channels m = j + 8k <= d need k <= d/8 (same for the whole warp)
-                const int kn = (d + 1) / kG;
                 const int dn = d < L ? d + 1 : d;
                 // all slots every degree (zeros where m > d): a degree-dependent
                 // bound here keeps more registers live and ran slower
@@ -252,7 +259,12 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(const float* __restrict__ 
                     ta[k] = na[k];
                     if (GRAD) tf[k] = nf[k];
                 }
+                ++d;
+                if (d > L) break;
+                if (MINRUN ? (d * d - l * l >= kCap - (SE - 1)) : ((d + 1) * (d + 1) - l * l > kCap - (SE - 1)))
+                    break;
             }
+            const int lw = d;
 
             // Send the window: per plane, the sector-aligned run [s, e) by one
             // bulk copy; the row head (first window) and the row tail (last
@@ -546,13 +558,14 @@ __global__ void __launch_bounds__(256) row_bwd_kernel(const float* __restrict__ 
     __syncwarp();
 }
 
-template <typename TO, bool GRAD, bool NORM, int NCH>
+template <typename TO, bool GRAD, bool NORM, int NCH, bool MINRUN>
 int launch_row(const FwdArgs& a) {
     const float* rt = static_cast<const float*>(device_row_tables());
     if (!rt) return int(cudaErrorMemoryAllocation);
-    auto kern = row_fwd_kernel<TO, GRAD, NORM, NCH>;
-    const size_t per_warp = row_warp_bytes<TO, GRAD>();
-    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : 1;  // measured: 1 >= 2 > 4 > 8
+    auto kern = row_fwd_kernel<TO, GRAD, NORM, NCH, MINRUN>;
+    const size_t per_warp = row_warp_bytes<TO, GRAD, NCH, MINRUN>();
+    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : 1;
+    if (W > kRowMaxWarps) return int(cudaErrorInvalidConfiguration);
     const size_t smem = size_t(W) * per_warp;
     if (smem > size_t(max_smem_optin())) return int(cudaErrorInvalidConfiguration);
     if (smem > 48 * 1024) {
@@ -616,11 +629,27 @@ int launch_row_bwd_flags(const BwdArgs& a, const float* tb) {
     return a.normalized ? launch_row_bwd<true, NCH>(a, tb) : launch_row_bwd<false, NCH>(a, tb);
 }
 
+// Window policy: launch.lanes_per_point 1 = windows that fit the buffer,
+// 2 = windows of at least kCap - SE columns (MINRUN, larger buffers), 0 = by
+// measurement on GB300 (200,000 points, l_max 16..63): FP32 rows keep the
+// smaller buffers (more warps per SM) except at l_max 28..31, where windows
+// that fit fall to ~160 columns (3.26 -> 3.55 TB/s at l_max 30); bf16 rows,
+// half the shared memory, take the longer runs (up to +13 % at l_max 63).
+inline bool row_minrun_default(int L, bool bf16) { return bf16 || (L >= 28 && L <= 31); }
+
+template <typename TO, int NCH, bool MINRUN>
+int launch_row_policy(const FwdArgs& a) {
+    const bool grad = a.dsph != nullptr, norm = a.normalized != 0;
+    if (grad)
+        return norm ? launch_row<TO, true, true, NCH, MINRUN>(a) : launch_row<TO, true, false, NCH, MINRUN>(a);
+    return norm ? launch_row<TO, false, true, NCH, MINRUN>(a) : launch_row<TO, false, false, NCH, MINRUN>(a);
+}
+
 template <typename TO, int NCH>
 int launch_row_flags(const FwdArgs& a) {
-    const bool grad = a.dsph != nullptr, norm = a.normalized != 0;
-    if (grad) return norm ? launch_row<TO, true, true, NCH>(a) : launch_row<TO, true, false, NCH>(a);
-    return norm ? launch_row<TO, false, true, NCH>(a) : launch_row<TO, false, false, NCH>(a);
+    const int pol = a.launch.lanes_per_point;
+    const bool minrun = pol == 2 || (pol == 0 && row_minrun_default(a.l_max, sizeof(TO) == 2));
+    return minrun ? launch_row_policy<TO, NCH, true>(a) : launch_row_policy<TO, NCH, false>(a);
 }
 
 template <int NCH>

@@ -191,6 +191,13 @@ def test_argument_errors_before_any_cuda_call():
         assert _err(C.sphericart_compute_ex, 16, 4, 30, 0, 0, 0, 0, k, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
         assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 0, k, launch, 16, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, 7, launch, 16, none, none, none) == C.SPH_EINVAL
+    # e3nn convention: bad normalization / dtype / l_max, NULL workspace
+    lib = C.lib()
+    assert lib.sphericart_compute_e3nn(16, 4, 8, 0, 3, 0, 16, 16, None, None) == C.SPH_EINVAL
+    assert lib.sphericart_compute_e3nn(16, 4, 8, 0, 0, 2, 16, 16, None, None) == C.SPH_EINVAL
+    assert lib.sphericart_compute_e3nn(16, 4, 129, 0, 0, 0, 16, 16, None, None) == C.SPH_EINVAL
+    assert lib.sphericart_compute_e3nn(16, 4, 8, 0, 0, 0, None, 16, None, None) == C.SPH_EINVAL
+    assert lib.sphericart_compute_e3nn(16, 0, 8, 0, 0, 0, None, None, None, None) == C.SPH_OK
     # POINT_HC (hard-coded l <= 3 + recursion): l_max <= 8, no Hessians, no bf16 storage
     hc = C.SPH_KERNEL_POINT_HC
     assert _err(C.sphericart_compute_ex, 16, 4, 9, 0, 0, 0, 0, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
