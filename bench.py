@@ -366,6 +366,7 @@ def main():
                  "hess", "degree50_f64"],
         help="launch only this kernel family warmup+steps times (for ncu), print a short line",
     )
+    ap.add_argument("--lmax", type=int, default=0, help="with --profile: l_max of the captured launches (0: the mode's own)")
     ap.add_argument("--dry-run", action="store_true",
                     help="host-only run of the multi-rank logic (gloo, no GPU): sharding, barrier, max over ranks")
     args = ap.parse_args()
@@ -585,6 +586,8 @@ def run_profile(args):
         L = 50
     else:
         L = BWD_L  # backward kernels and the expansion: l_max = 6
+    if args.lmax > 0 and args.profile not in ("batch", "batched"):
+        L = args.lmax
     K = (L + 1) ** 2
     x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=8)).to(dev)
     if args.profile == "fwd":

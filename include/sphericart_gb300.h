@@ -125,15 +125,21 @@ typedef enum {
  *   points_per_tile  points a warp computes per tile, 4..32, multiple of 4
  *   warps_per_block  independent warps per CTA, 1..8
  *   blocks_per_sm    resident CTAs per SM to size the persistent grid (0 = max)
- *   lanes_per_point  SLICE kernels only: 8, 16 or 32 (0 = by l_max)
+ *   lanes_per_point  POINT: 0 (default), 1, or 4 = one lane per output plane
+ *                    (value, d/dx, d/dy, d/dz) of each point, points_per_tile
+ *                    <= 8: every lane busy where one-lane tiles that fit
+ *                    shared memory are short (FP32 arithmetic, gradients, no
+ *                    Hessians); SLICE: 8, 16 or 32 (0 = by l_max)
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
  * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
  * (forward 0..2, backward 0..8; 0 = 1 forward, 2 backward) and blocks_per_sm.
  * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
  * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
- * the FP64 pipe); when a call has fewer than 2 x SMs x warps_per_block tiles,
- * it runs fewer warps per block so that the blocks reach every SM.          */
+ * the FP64 pipe), and with FP32 gradients from l_max 10 runs 4 lanes per
+ * point on 8-point tiles; when a call has fewer than 2 x SMs x
+ * warps_per_block tiles, it runs fewer warps per block so that the blocks
+ * reach every SM.                                                           */
 typedef struct {
     int32_t points_per_tile;
     int32_t warps_per_block;
@@ -455,12 +461,13 @@ int sphericart_batch_autotune(const sph_batch_set* sets, int nsets, void* stream
                               int reps, sph_launch* best, float* best_ms);
 
 /* sphericart_tune_export: writes the tuned POINT shapes of the current device
- * as text lines "gpu_name l_max dtype out grad P W B" into buf (NUL-terminated,
+ * as text lines "gpu_name l_max dtype out grad P W B lanes" into buf (NUL-terminated,
  * truncated to len); *needed receives the full size. Host memory. */
 int sphericart_tune_export(char* buf, size_t len, size_t* needed);
 
 /* sphericart_tune_import: installs the lines of `text` whose gpu_name matches
- * the current device (others are skipped); *imported receives the count. */
+ * the current device (others are skipped; a missing lanes field reads as 0);
+ * *imported receives the count. */
 int sphericart_tune_import(const char* text, int* imported);
 
 /* sphericart_fma_peak: measures this device's fused multiply-add throughput

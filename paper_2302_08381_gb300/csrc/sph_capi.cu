@@ -275,6 +275,30 @@ sph_launch default_point_fwd(int L, int grad, int elem, int hess = 0) {
     return sph_launch{P, W, 0, 0};
 }
 
+// Shared-memory bytes per point of the 4-lanes-per-point POINT tile: a value
+// row and 3 gradient rows, each of stride K (odd K) or K + 1 (even K).
+size_t point4_row_bytes(int L, int elem) {
+    const size_t K = size_t(L + 1) * size_t(L + 1);
+    return size_t(elem) * 4 * ((K % 2 == 0) ? K + 1 : K);
+}
+
+// Default shape of the 4-lanes-per-point tile: 8 points per warp (all 32
+// lanes). Measured on GB300 (1M points, FP32 gradients, l_max 10..16): odd K
+// (bulk-copied tiles) is fastest with 4-warp blocks on a grid of 16 blocks
+// per SM in waves, even K (warp copy-out) with 2-warp blocks in one wave.
+sph_launch default_point4_fwd(int L, int elem) {
+    (void)elem;
+    const int K = (L + 1) * (L + 1);
+    return K % 2 ? sph_launch{8, 4, 16, 4} : sph_launch{8, 2, 0, 4};
+}
+
+// Whether the POINT default (no shape given, none tuned) runs 4 lanes per
+// point: FP32 arithmetic with gradients, no Hessians, l_max >= 10 (where the
+// one-lane tile that fits shared memory leaves most lanes idle).
+bool point4_default(int L, int grad, int elem, int hess, int hc) {
+    return grad && !hess && !hc && elem != 8 && L >= 10;
+}
+
 sph_launch default_point_bwd(int L, int elem, int dbw) {
     const size_t K = size_t(L + 1) * (L + 1);
     const size_t V = (K % 2 == 0) ? K + 1 : K;
@@ -546,14 +570,33 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             cudaGetDevice(&d);
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, ddsph ? 2 : grad});
-            if (it != g_tuned.end()) {
+            if (it != g_tuned.end() && !(hc && it->second.lanes_per_point == 4)) {
                 a.launch = it->second;
                 from_default = false;
             }
         }
         const int hess = ddsph ? 1 : 0;
-        const sph_launch dflt = default_point_fwd(l_max, grad, eo, hess);
-        if (!resolve_point(a.launch, dflt, l_max, eo, point_row_bytes(l_max, grad, eo, hess))) return SPH_EINVAL;
+        if (from_default && a.launch.points_per_tile == 0 && a.launch.warps_per_block == 0 &&
+            a.launch.blocks_per_sm == 0 && a.launch.lanes_per_point == 0 &&
+            point4_default(l_max, grad, eo, hess, hc))
+            a.launch.lanes_per_point = 4;
+        const int lpp = a.launch.lanes_per_point;
+        if (lpp != 0 && lpp != 1 && lpp != 4) {
+            set_error("POINT launch: lanes_per_point must be 0, 1 or 4");
+            return SPH_EINVAL;
+        }
+        if (lpp == 4 && (!grad || hess || dtype != SPH_F32 || hc)) {
+            set_error("POINT with 4 lanes per point takes FP32 arithmetic, values and gradients (no Hessians)");
+            return SPH_EUNSUPPORTED;
+        }
+        const sph_launch dflt = lpp == 4 ? default_point4_fwd(l_max, eo) : default_point_fwd(l_max, grad, eo, hess);
+        if (!resolve_point(a.launch, dflt, l_max, eo,
+                           lpp == 4 ? point4_row_bytes(l_max, eo) : point_row_bytes(l_max, grad, eo, hess)))
+            return SPH_EINVAL;
+        if (lpp == 4 && a.launch.points_per_tile > 8) {
+            set_error("POINT with 4 lanes per point: points_per_tile must be <= 8 (32 lanes per warp)");
+            return SPH_EINVAL;
+        }
         if (from_default) {
             // Few tiles (small n): fewer warps per block, so that the blocks
             // spread over every SM instead of filling a few (measured at 10k
@@ -768,7 +811,12 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
             auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, hess ? 2 : (grad ? 1 : 0)});
             if (it != g_tuned.end()) s = it->second;
         }
-        const sph_launch dflt = default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
+        const bool four = s.lanes_per_point == 4 ||
+                          (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0 &&
+                           s.lanes_per_point == 0 && point4_default(l_max, grad, eo, hess, hc ? 1 : 0));
+        const sph_launch dflt =
+            four ? default_point4_fwd(l_max, eo) : default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
+        if (four) s.lanes_per_point = 4;
         // as resolve_point: no tuned shape at all takes the whole default
         if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = dflt.blocks_per_sm;
         if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;
@@ -792,9 +840,25 @@ int sphericart_set_launch(int l_max, int dtype, int out, int grad, const sph_lau
     const int eo = elem_size(dtype, out);
     const int g = grad >= 2 ? 2 : (grad ? 1 : 0);  // 2: values + gradients + Hessians
     sph_launch s = *launch;
-    if (!resolve_point(s, default_point_fwd(l_max, g ? 1 : 0, eo, g == 2), l_max, eo,
-                       point_row_bytes(l_max, g ? 1 : 0, eo, g == 2)))
+    if (s.lanes_per_point != 0 && s.lanes_per_point != 1 && s.lanes_per_point != 4) {
+        set_error("set_launch: POINT lanes_per_point must be 0, 1 or 4");
         return SPH_EINVAL;
+    }
+    if (s.lanes_per_point == 4) {
+        if (g != 1 || dtype != SPH_F32) {
+            set_error("set_launch: 4 lanes per point take FP32 arithmetic, values and gradients");
+            return SPH_EINVAL;
+        }
+        if (!resolve_point(s, default_point4_fwd(l_max, eo), l_max, eo, point4_row_bytes(l_max, eo)))
+            return SPH_EINVAL;
+        if (s.points_per_tile > 8) {
+            set_error("set_launch: 4 lanes per point take points_per_tile <= 8");
+            return SPH_EINVAL;
+        }
+    } else if (!resolve_point(s, default_point_fwd(l_max, g ? 1 : 0, eo, g == 2), l_max, eo,
+                              point_row_bytes(l_max, g ? 1 : 0, eo, g == 2))) {
+        return SPH_EINVAL;
+    }
     int d = -1;
     cudaGetDevice(&d);
     std::lock_guard<std::mutex> lk(g_mu);

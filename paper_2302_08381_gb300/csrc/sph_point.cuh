@@ -347,6 +347,184 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
     if (bulk && lane == 0) bulk_wait_all();
 }
 
+// -------------------------------------- forward, 4 lanes per point (planes)
+// POINT with lanes_per_point = 4 (values and gradients): lane 4j + r of a
+// warp owns output plane r (0 the value, 1..3 d/dx, d/dy, d/dz) of the tile's
+// point j, so a tile of 8 points keeps all 32 lanes busy where the
+// one-lane-per-point tile that fits shared memory at large l_max holds only
+// 8 to 16 points. Every lane runs the Q recursion (Eq. iter-q) and Eq.
+// iter-sc in full (cheap next to the assembly) and assembles only its plane
+// with role weights, the same instruction stream in every lane:
+//   plane = A c_m + m Qtilde_l^m C'_m,   A = a0 Qtilde + ax e Qtilde_{l-1}^{m+1} + a3 f Qtilde_{l-1}^m
+// (a0, ax, a3) = (1, 0, 0), (0, x, 0), (0, y, 0), (0, 0, 1) by role, and
+// C'_m = c_{m-1} (d/dx), -s_{m-1} (d/dy), 0 (value, d/dz); the sin-type column
+// takes s_m and S'_m = s_{m-1}, c_{m-1}, 0. These are the terms of Eq.
+// iter-deri that assemble_m combines for all four planes at once.
+template <int L, bool NORM, typename T, typename TO>
+__device__ __forceinline__ void point4_core(T x, T y, T z, T r2, const PointTabs<L, T, false>& tb, int r, T ir,
+                                            TO* __restrict__ rowp) {
+    const T a0 = r == 0 ? T(1) : T(0);
+    const T ax = r == 1 ? x : (r == 2 ? y : T(0));
+    const T a3 = r == 3 ? T(1) : T(0);
+    const T a00 = a0 * tb.inv_sqrt2;  // m = 0 value: Qtilde_l^0 / sqrt2
+    T c[L + 1], s[L + 1];
+    point_cs<L>(x, y, c, s);
+    T c1[L + 1], s1[L + 1];  // (C'_m, S'_m) of this lane's role
+    {
+        const T k1 = r == 1 ? T(1) : T(0), k2 = r == 2 ? T(-1) : T(0);
+        const T k3 = r == 2 ? T(1) : T(0), k4 = r == 1 ? T(1) : T(0);
+        c1[0] = T(0);
+        s1[0] = T(0);
+#pragma unroll
+        for (int m = 1; m <= L; ++m) {
+            c1[m] = k1 * c[m - 1] + k2 * s[m - 1];
+            s1[m] = k3 * c[m - 1] + k4 * s[m - 1];
+        }
+    }
+    // Normalized form (x, y, z = u): plane' = irr (plane - l u_r value), with
+    // u_r = 0 and irr = 1 for the value plane.
+    const T nu = NORM ? -(r == 1 ? x : (r == 2 ? y : (r == 3 ? z : T(0)))) : T(0);
+    const T irr = (NORM && r != 0) ? ir : T(1);
+    T q1[L + 1], q2[L + 1];
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        q1[m] = T(0);
+        q2[m] = T(0);
+    }
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+        T q[L + 1];
+        q[l] = tb.qll[l];
+        if (l >= 1) q[l - 1] = tb.d[l] * z * q1[l - 1];
+#pragma unroll
+        for (int m = 0; m + 2 <= l; ++m) {  // Eq. iter-q, folded
+            const int i = tri(l, m);
+            q[m] = (tb.a[i] * z) * q1[m] - (tb.b[i] * r2) * q2[m];
+        }
+        const T nl = nu * T(l);
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            const int i = tri(l, m);
+            const T E1 = (m + 1 <= l - 1) ? tb.e[i] * q1[m + 1] : T(0);
+            const T Qz = (m <= l - 1) ? tb.fz[i] * q1[m] : T(0);
+            if (m == 0) {
+                T out = a00 * q[0] + ax * E1 + a3 * Qz;
+                if (NORM) out = irr * fma(nl, q[0] * tb.inv_sqrt2, out);
+                rowp[l * l + l] = OutConv<TO>::cv(out);
+            } else {
+                const T A = a0 * q[m] + ax * E1 + a3 * Qz;
+                const T mQ = T(m) * q[m];
+                T oc = A * c[m] + mQ * c1[m];
+                T os = A * s[m] + mQ * s1[m];
+                if (NORM) {
+                    oc = irr * fma(nl, q[m] * c[m], oc);
+                    os = irr * fma(nl, q[m] * s[m], os);
+                }
+                rowp[l * l + l + m] = OutConv<TO>::cv(oc);
+                rowp[l * l + l - m] = OutConv<TO>::cv(os);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            q2[m] = q1[m];
+            q1[m] = q[m];
+        }
+    }
+}
+
+// Shared-memory image of a 4-lane tile: P value rows and 3P gradient plane
+// rows, stride K (odd K: the image of the global range, sent by bulk copies)
+// or K + 1 (even K: copied out by the warp with coalesced stores).
+template <int L>
+struct Row4 {
+    static constexpr int K = (L + 1) * (L + 1);
+    static constexpr bool PAD = (K % 2 == 0);
+    static constexpr int S = PAD ? K + 1 : K;
+};
+
+template <int L, typename TO>
+__host__ __device__ constexpr size_t point4_warp_bytes(int P) {
+    return align16(size_t(P) * Row4<L>::S * sizeof(TO)) + align16(size_t(3 * P) * Row4<L>::S * sizeof(TO));
+}
+
+template <int L, bool NORM, typename T, typename TO>
+__global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ xyz, int64_t n,
+                                                         const __grid_constant__ PointTabs<L, T, false> tb,
+                                                         TO* __restrict__ sph, TO* __restrict__ dsph, int P,
+                                                         int bulk) {
+    constexpr int K = (L + 1) * (L + 1);
+    constexpr int S = Row4<L>::S;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int pt = lane >> 2, r = lane & 3;
+    TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point4_warp_bytes<L, TO>(P));
+    TO* s_d = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_v) + align16(size_t(P) * S * sizeof(TO)));
+    TO* rowp = r == 0 ? s_v + size_t(pt) * S : s_d + size_t(3 * pt + r - 1) * S;
+
+    const int64_t ntiles = (n + P - 1) / P;
+    const int64_t stride = int64_t(gridDim.x) * W;
+    int64_t tile = int64_t(blockIdx.x) * W + warp;
+    T nx = T(0), ny = T(0), nz = T(0);
+    if (tile < ntiles && pt < P) {
+        const int64_t p = tile * P + pt;
+        if (p < n) {
+            nx = xyz[3 * p];
+            ny = xyz[3 * p + 1];
+            nz = xyz[3 * p + 2];
+        }
+    }
+    for (; tile < ntiles; tile += stride) {
+        T x = nx, y = ny, z = nz;
+        const int64_t nt = tile + stride;
+        if (nt < ntiles && pt < P) {
+            const int64_t p = nt * P + pt;
+            if (p < n) {
+                nx = xyz[3 * p];
+                ny = xyz[3 * p + 1];
+                nz = xyz[3 * p + 2];
+            }
+        }
+        const int64_t p0 = tile * P;
+        const int cnt = int(min(int64_t(P), n - p0));
+        if (pt < cnt) {
+            T r2, ir = T(1);
+            if (NORM) {
+                unit_point(x, y, z, r2, ir);
+            } else {
+                r2 = x * x + y * y + z * z;
+            }
+            point4_core<L, NORM>(x, y, z, r2, tb, r, ir, rowp);
+        }
+        if constexpr (Row4<L>::PAD) {
+            __syncwarp();
+            warp_rows_out<K>(sph + p0 * K, s_v, cnt, S, lane);
+            warp_rows_out<K>(dsph + p0 * 3 * K, s_d, 3 * cnt, S, lane);
+            __syncwarp();
+            continue;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        const int64_t ev = int64_t(cnt) * K;
+        int64_t ev_bulk = 0, ed_bulk = 0;
+        if (bulk) {
+            ev_bulk = (ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
+            ed_bulk = (3 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
+            if (lane == 0) {
+                if (ev_bulk) bulk_store(sph + p0 * K, s_v, uint32_t(ev_bulk * sizeof(TO)));
+                if (ed_bulk) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * sizeof(TO)));
+                bulk_commit();
+            }
+        }
+        for (int64_t i = ev_bulk + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
+        for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
+        if (bulk && lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    }
+    if (bulk && lane == 0) bulk_wait_all();
+}
+
 // ----------------------------------------------------------------- backward
 // Loads the [cnt, K] tile of `src` at element offset `off` into `dst`: the
 // 16-byte-multiple prefix by a bulk copy on `bar` (if `bulk`), the rest with
@@ -651,6 +829,24 @@ int launch_point_fwd(const FwdArgs& a) {
     kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
         static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph),
         static_cast<TO*>(a.ddsph), P, bulk ? 1 : 0);
+    return int(cudaGetLastError());
+}
+
+// POINT forward with 4 lanes per point (values and gradients); P <= 8 and W
+// resolved by the caller.
+template <int L, bool NORM, typename T, typename TO>
+int launch_point4_fwd(const FwdArgs& a) {
+    static const PointTabs<L, T, false> tb = make_point_tabs<L, T, false>();
+    const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
+    const size_t smem = size_t(W) * point4_warp_bytes<L, TO>(P);
+    auto kern = point4_fwd_kernel<L, NORM, T, TO>;
+    cudaError_t err = ensure_smem(kern, smem);
+    if (err != cudaSuccess) return int(err);
+    const int64_t ntiles = ceil_div(a.n, P);
+    const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
+    const bool bulk = (reinterpret_cast<uintptr_t>(a.sph) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0);
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph), P, bulk ? 1 : 0);
     return int(cudaGetLastError());
 }
 

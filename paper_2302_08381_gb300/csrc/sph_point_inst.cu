@@ -21,6 +21,13 @@ int SPH_CAT(point_fwd_L, SPH_INST_L)(const FwdArgs& a) {
                         : launch_point_fwd<L, true, false, false, T, TO>(a))    \
                 : (norm ? launch_point_fwd<L, false, false, true, T, TO>(a)     \
                         : launch_point_fwd<L, false, false, false, T, TO>(a));
+    if (a.launch.lanes_per_point == 4) {  // one lane per output plane (FP32 arithmetic, gradients)
+        if (!grad || a.ddsph != nullptr || a.dtype != SPH_F32) return int(cudaErrorInvalidValue);
+        if (a.out == SPH_OUT_BF16)
+            return norm ? launch_point4_fwd<L, true, float, __nv_bfloat16>(a)
+                        : launch_point4_fwd<L, false, float, __nv_bfloat16>(a);
+        return norm ? launch_point4_fwd<L, true, float, float>(a) : launch_point4_fwd<L, false, float, float>(a);
+    }
     if (a.ddsph != nullptr) {  // Hessians (FP32 or FP64 storage; validated by the caller)
         if (a.dtype == SPH_F64)
             return norm ? launch_point_fwd<L, true, true, true, double, double>(a)

@@ -155,13 +155,17 @@ int sphericart_autotune(const void* xyz, int64_t n, int l_max, int normalized, i
     const int Bs[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};  // > occupancy: blocks scheduled in waves
     // the POINT variant AUTO runs for this request (both take the same shapes)
     const int fam = point_hybrid_wins(l_max, dtype, grad != 0) ? SPH_KERNEL_POINT_HC : SPH_KERNEL_POINT;
+    // one lane per point (lanes_per_point 1), then, for FP32 arithmetic with
+    // gradients, one lane per output plane (lanes_per_point 4, <= 8 points)
+    const bool four = grad && dtype == SPH_F32 && fam == SPH_KERNEL_POINT;
+    for (int pass = 0; pass < (four ? 2 : 1); ++pass)
     for (int P : Ps) {
-        if (P % mult != 0) continue;
+        if (P % mult != 0 || (pass == 1 && P > 8)) continue;
         for (int W : Ws) {
             const size_t smem = size_t(W) * (size_t(P) * row + 64);
             if (smem > size_t(max_smem_optin())) continue;
             for (int B : Bs) {
-                sph_launch s{P, W, B, 0};
+                sph_launch s{P, W, B, pass == 1 ? 4 : 0};
                 int stt = sphericart_compute_ex(xyz, n, l_max, normalized, dtype, out, SPH_Q_NATIVE, fam, &s, sph,
                                                 dsph, nullptr, stream);
                 if (stt != SPH_OK) {
@@ -271,7 +275,7 @@ int sphericart_tune_export(char* buf, size_t len, size_t* needed) {
                     if (!tuned_launch(L, dt, out, grad, &s)) continue;
                     (void)fam;
                     os << name << ' ' << L << ' ' << dt << ' ' << out << ' ' << grad << ' ' << s.points_per_tile
-                       << ' ' << s.warps_per_block << ' ' << s.blocks_per_sm << '\n';
+                       << ' ' << s.warps_per_block << ' ' << s.blocks_per_sm << ' ' << s.lanes_per_point << '\n';
                 }
     const std::string text = os.str();
     if (needed) *needed = text.size() + 1;
@@ -298,7 +302,9 @@ int sphericart_tune_import(const char* text, int* imported) {
         int L, dt, out, grad, P, W, B;
         if (!(ls >> gpu >> L >> dt >> out >> grad >> P >> W >> B)) continue;
         if (gpu != name) continue;
-        sph_launch s{P, W, B, 0};
+        int lanes = 0;  // optional 9th field: lanes_per_point
+        if (!(ls >> lanes)) lanes = 0;
+        sph_launch s{P, W, B, lanes};
         if (sphericart_set_launch(L, dt, out, grad, &s) == SPH_OK) ++count;
     }
     if (imported) *imported = count;
