@@ -765,6 +765,16 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True, kernel="slice"), 4, 13),
         (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
         (1_000_000, 10, "l10_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
+        # l_max 12..16 (AUTO: 4 lanes per point, one per output plane) against
+        # the best one-lane-per-point shapes measured on this GPU
+        (1_000_000, 12, "l12_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 12, "l12_grad_f32_n1M_one_lane", dict(gradients=True, kernel="point", launch=(16, 1, 0, 1)), 4, 4),
+        (1_000_000, 13, "l13_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 14, "l14_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 15, "l15_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 16, "l16_grad_f32_n1M", dict(gradients=True), 4, 4),
+        (1_000_000, 16, "l16_grad_f32_n1M_one_lane", dict(gradients=True, kernel="point", launch=(8, 2, 0, 1)), 4, 4),
+        (1_000_000, 16, "l16_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
         # the paper's GPU table sizes (10k / 100k points, l_max = 8)
         (10_000, 8, "l8_values_f64_n10k", dict(), 8, 1),
         (10_000, 8, "l8_values_f64_n10k_normalized", dict(normalized=True), 8, 1),
@@ -799,6 +809,10 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         dt = torch.float64 if elem == 8 else torch.float32
         x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=2)).to(dev, dt)
         K = (L + 1) ** 2
+        if isinstance(kw.get("launch"), tuple):
+            from paper_2302_08381_gb300 import _capi as C
+
+            kw = dict(kw, launch=C.make_launch(*kw["launch"]))
 
         def fn():
             api.spherical_harmonics(x, L, **kw)

@@ -104,7 +104,11 @@ int one_shapes(int grad, const sph_launch& lau, int nsets, OneShapes* out) {
             P = point_fwd_shape(L, grad).points_per_tile;
         }
         P = std::max(P, mult);
-        const size_t bytes = align128(size_t(P) * V * 4) + (grad ? align128(size_t(P) * D * 4) : 0);
+        size_t bytes = align128(size_t(P) * V * 4) + (grad ? align128(size_t(P) * D * 4) : 0);
+        if (grad && L >= kPoint4MinL) {  // 4 lanes per point (one_four): 8-point tiles
+            P = 8;
+            bytes = point4_tile_bytes(L, 4, P, 128);
+        }
         const int W = int(std::min<size_t>(size_t(max_warps), S / bytes));
         if (W < 1) {
             set_error("batch one-launch: a %d-point tile at l_max %d needs %zu bytes of shared memory", P, L, bytes);
@@ -358,6 +362,10 @@ int sphericart_batch_plan_create_ex(const sph_batch_set* sets, int nsets, const 
         P = std::max(mult, P / mult * mult);
         if (class_shapes) P = point_fwd_shape(L, grad).points_per_tile;  // a multiple of mult, <= 32
         bytes_of[hs.size()] = int(align16(size_t(P) * V * 4) + (grad ? align16(size_t(P) * D * 4) : 0));
+        if (mode == SPH_BATCH_PER_LMAX && grad && L >= kPoint4MinL) {  // 4 lanes per point (batch_four)
+            P = 8;
+            bytes_of[hs.size()] = int(point4_tile_bytes(L, 4, P, 16));
+        }
         BatchSet b{};
         b.xyz = s.xyz;
         b.sph = s.sph;
@@ -390,6 +398,8 @@ int sphericart_batch_plan_create_ex(const sph_batch_set* sets, int nsets, const 
         bl.tile_end = (j < nsets) ? hs[j].tile_begin : tiles;
         bl.per_warp_bytes = bytes;
         bl.W = class_shapes ? point_fwd_shape(hs[i].L, hs[i].dsph ? 1 : 0).warps_per_block : W;
+        if (class_shapes && mode == SPH_BATCH_PER_LMAX && hs[i].dsph && hs[i].L >= kPoint4MinL)
+            bl.W = point4_default_warps(hs[i].L);
         bl.smem = size_t(bl.W) * size_t(bytes);
         if (bl.smem > size_t(max_smem_optin())) {
             set_error("batch plan needs %zu bytes of shared memory per block", bl.smem);

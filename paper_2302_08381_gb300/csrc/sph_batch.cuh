@@ -49,6 +49,14 @@ struct BatchVis {
     }
 };
 
+// Per-class launches (flags fixed at compile time) with gradients from
+// l_max kPoint4MinL run 4 lanes per point (one per output plane, tiles of
+// <= 8 points); every other tile one lane per point.
+template <int L, int GN>
+__host__ __device__ constexpr bool batch_four() {
+    return GN >= 0 && (GN & 1) != 0 && L >= kPoint4MinL;
+}
+
 template <int L, int GN>
 __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigned char* buf,
                                            const PointTabs<16, float, false>& tb, int lane, float px, float py,
@@ -58,6 +66,10 @@ __device__ __forceinline__ void batch_tile(const BatchSet& s, int64_t t, unsigne
     const int P = s.P;
     const int64_t p0 = t * P;
     const int cnt = int(min(int64_t(P), s.n - p0));
+    if constexpr (batch_four<L, GN>()) {
+        point4_tile<L, (GN & 2) != 0>(s.sph, s.dsph, p0, cnt, P, s.bulk, buf, tb, lane, px, py, pz);
+        return;
+    }
     float* s_v = reinterpret_cast<float*>(buf);
     float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * RS::V * 4));
     const bool grad = GN < 0 ? s.dsph != nullptr : (GN & 1) != 0;
@@ -153,9 +165,10 @@ __global__ void __launch_bounds__(256) batch_kernel_t(const BatchSet* __restrict
             s_end = (si + 1 < set_end) ? sets[si + 1].tile_begin : tile_end;
         }
     };
+    const int me = (FIXL >= 0 && batch_four<(FIXL >= 0 ? FIXL : 0), GN>()) ? lane >> 2 : lane;  // lane's point
     auto prefetch = [&](int64_t t, float& x, float& y, float& z) {
-        const int64_t p = (t - s.tile_begin) * s.P + lane;
-        if (lane < s.P && p < s.n) {
+        const int64_t p = (t - s.tile_begin) * s.P + me;
+        if (me < s.P && p < s.n) {
             x = s.xyz[3 * p];
             y = s.xyz[3 * p + 1];
             z = s.xyz[3 * p + 2];
@@ -200,7 +213,7 @@ __global__ void __launch_bounds__(256) batch_kernel_t(const BatchSet* __restrict
         }
         t = tn;
     }
-    if (lane == 0) bulk_wait_all();
+    bulk_wait_all();  // every lane: 4-lane tiles of some l_max send one row per lane
 }
 
 // Host tables of Eq. iter-q / iter-deri for l <= 16 as a kernel parameter.

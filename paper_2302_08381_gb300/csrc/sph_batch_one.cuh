@@ -76,6 +76,13 @@ struct OneSet {
     int bulk;
 };
 
+// Classes with gradients from l_max kPoint4MinL run 4 lanes per point (one
+// per output plane, tiles of <= 8 points); the others one lane per point.
+template <int L, int GN>
+__host__ __device__ constexpr bool one_four() {
+    return (GN & 1) != 0 && L >= kPoint4MinL;
+}
+
 template <int L, int GN>
 __device__ __forceinline__ void one_tile(const OneSet& s, int64_t t, unsigned char* buf,
                                          const PointTabs<16, float, false>& tb, int lane, float px, float py,
@@ -87,6 +94,10 @@ __device__ __forceinline__ void one_tile(const OneSet& s, int64_t t, unsigned ch
     const int P = s.P;
     const int64_t p0 = t * P;
     const int cnt = int(min(int64_t(P), s.n - p0));
+    if constexpr (one_four<L, GN>()) {
+        point4_tile<L, NORM>(s.sph, s.dsph, p0, cnt, P, s.bulk, buf, tb, lane, px, py, pz);
+        return;
+    }
     float* s_v = reinterpret_cast<float*>(buf);
     float* s_d = reinterpret_cast<float*>(buf + align128(size_t(P) * RS::V * 4));
     // Rows lane, lane + 32, ...: the next row's coordinates are loaded while
@@ -181,9 +192,10 @@ __device__ __forceinline__ void one_class(const sph_batch_set* __restrict__ desc
                          : 0;
         }
     };
+    const int me = one_four<L, GN>() ? lane >> 2 : lane;  // this lane's point of a tile
     auto prefetch = [&](int64_t t, float& x, float& y, float& z) {
-        const int64_t q = (t - s.base) * P + lane;
-        if (lane < P && q < s.n) {
+        const int64_t q = (t - s.base) * P + me;
+        if (me < P && q < s.n) {
             x = s.xyz[3 * q];
             y = s.xyz[3 * q + 1];
             z = s.xyz[3 * q + 2];
@@ -323,12 +335,13 @@ __global__ void __launch_bounds__(32 * kOneMaxWarps, 1)
                     break;
             }
             // the next class lays its buffers out differently: every bulk
-            // store of this warp must have read its buffer
-            if (lane == 0) bulk_wait_read_all();
+            // store of this warp must have read its buffer (4-lane tiles of
+            // some l_max send one row per lane)
+            bulk_wait_read_all();
         }
         __syncthreads();
     }
-    if (lane == 0) bulk_wait_all();
+    bulk_wait_all();
 
     // ---- the last block to finish returns the counters to zero
     __syncthreads();

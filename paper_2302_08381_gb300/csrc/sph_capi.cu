@@ -276,27 +276,22 @@ sph_launch default_point_fwd(int L, int grad, int elem, int hess = 0) {
 }
 
 // Shared-memory bytes per point of the 4-lanes-per-point POINT tile: a value
-// row and 3 gradient rows, each of stride K (odd K) or K + 1 (even K).
-size_t point4_row_bytes(int L, int elem) {
-    const size_t K = size_t(L + 1) * size_t(L + 1);
-    return size_t(elem) * 4 * ((K % 2 == 0) ? K + 1 : K);
-}
+// row and 3 gradient rows of stride point4_stride.
+size_t point4_row_bytes(int L, int elem) { return size_t(elem) * 4 * size_t(point4_stride(L, elem)); }
 
 // Default shape of the 4-lanes-per-point tile: 8 points per warp (all 32
-// lanes). Measured on GB300 (1M points, FP32 gradients, l_max 10..16): odd K
-// (bulk-copied tiles) is fastest with 4-warp blocks on a grid of 16 blocks
-// per SM in waves, even K (warp copy-out) with 2-warp blocks in one wave.
+// lanes), point4_default_warps warps per block, a grid of 16 blocks per SM
+// scheduled in waves (measured on GB300, 1M points, FP32 gradients).
 sph_launch default_point4_fwd(int L, int elem) {
     (void)elem;
-    const int K = (L + 1) * (L + 1);
-    return K % 2 ? sph_launch{8, 4, 16, 4} : sph_launch{8, 2, 0, 4};
+    return sph_launch{8, point4_default_warps(L), 16, 4};
 }
 
 // Whether the POINT default (no shape given, none tuned) runs 4 lanes per
 // point: FP32 arithmetic with gradients, no Hessians, l_max >= 10 (where the
 // one-lane tile that fits shared memory leaves most lanes idle).
 bool point4_default(int L, int grad, int elem, int hess, int hc) {
-    return grad && !hess && !hc && elem != 8 && L >= 10;
+    return grad && !hess && !hc && elem != 8 && L >= kPoint4MinL;
 }
 
 sph_launch default_point_bwd(int L, int elem, int dbw) {

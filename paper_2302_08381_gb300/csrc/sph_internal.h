@@ -96,6 +96,43 @@ struct FwdArgs {
     int hc = 0;          // POINT: hard-coded degrees l <= 3, then the recursion (l_max <= kHcMaxL)
 };
 
+// Smallest l_max at which FP32 gradient tiles run 4 lanes per point (one per
+// output plane) by default, in single-set launches and in ragged batches.
+constexpr int kPoint4MinL = 10;
+
+// Shared-memory row stride (elements) of the 4-lanes-per-point POINT tile
+// and how the tile leaves shared memory:
+//   odd K: stride K, the image of the global range, one bulk copy per array;
+//   even K with 16-byte rows (K * elem % 16 == 0): a stride of an odd number
+//     of 16-byte units (K itself when K * elem / 16 is odd: again the image
+//     of the global range), so that 32 lanes writing one column hit 8 banks
+//     and every row can leave by its own bulk copy;
+//   otherwise: stride K + 1 (conflict-free), copied out by the warp.
+SPH_HD constexpr int point4_stride(int L, int elem) {
+    const int K = (L + 1) * (L + 1);
+    if (K % 2) return K;
+    if ((K * elem) % 16) return K + 1;
+    return ((K * elem / 16) % 2) ? K : K + 16 / elem;
+}
+// Staged bytes of a 4-lanes-per-point tile of P points (value rows, then
+// gradient rows, each part rounded up to `align` bytes).
+inline size_t point4_tile_bytes(int L, int elem, int P, size_t align) {
+    const size_t S = size_t(point4_stride(L, elem)) * size_t(elem);
+    const size_t v = (size_t(P) * S + align - 1) / align * align;
+    const size_t d = (size_t(3 * P) * S + align - 1) / align * align;
+    return v + d;
+}
+
+// 0: whole-tile bulk copies, 1: one bulk copy per row, 2: warp copy-out.
+SPH_HD constexpr int point4_out_mode(int L, int elem) {
+    const int K = (L + 1) * (L + 1);
+    return point4_stride(L, elem) == K ? 0 : ((K * elem) % 16 ? 2 : 1);
+}
+// Warps per block of the default 4-lanes-per-point shape (measured on GB300,
+// 1M points, FP32, l_max 10..16, grid of 16 blocks per SM in waves): 4, and
+// 2 where every row leaves by its own bulk copy.
+inline int point4_default_warps(int L) { return point4_out_mode(L, 4) == 1 ? 2 : 4; }
+
 // Largest l_max with the hybrid POINT forward (hard-coded l <= 3) compiled.
 constexpr int kHcMaxL = 8;
 

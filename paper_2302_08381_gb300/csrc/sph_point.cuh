@@ -360,8 +360,8 @@ __global__ void __launch_bounds__(256) point_fwd_kernel(const T* __restrict__ xy
 // C'_m = c_{m-1} (d/dx), -s_{m-1} (d/dy), 0 (value, d/dz); the sin-type column
 // takes s_m and S'_m = s_{m-1}, c_{m-1}, 0. These are the terms of Eq.
 // iter-deri that assemble_m combines for all four planes at once.
-template <int L, bool NORM, typename T, typename TO>
-__device__ __forceinline__ void point4_core(T x, T y, T z, T r2, const PointTabs<L, T, false>& tb, int r, T ir,
+template <int L, bool NORM, typename T, typename TO, typename Tabs>
+__device__ __forceinline__ void point4_core(T x, T y, T z, T r2, const Tabs& tb, int r, T ir,
                                             TO* __restrict__ rowp) {
     const T a0 = r == 0 ? T(1) : T(0);
     const T ax = r == 1 ? x : (r == 2 ? y : T(0));
@@ -433,18 +433,82 @@ __device__ __forceinline__ void point4_core(T x, T y, T z, T r2, const PointTabs
 }
 
 // Shared-memory image of a 4-lane tile: P value rows and 3P gradient plane
-// rows, stride K (odd K: the image of the global range, sent by bulk copies)
-// or K + 1 (even K: copied out by the warp with coalesced stores).
-template <int L>
+// rows of stride S (point4_stride): MODE 0 the image of the global ranges
+// (one bulk copy per array), 1 rows at 16-byte-aligned strides (one bulk copy
+// per row, issued by the lane that wrote it), 2 padded rows copied out by the
+// warp with coalesced stores.
+template <int L, typename TO>
 struct Row4 {
     static constexpr int K = (L + 1) * (L + 1);
-    static constexpr bool PAD = (K % 2 == 0);
-    static constexpr int S = PAD ? K + 1 : K;
+    static constexpr int S = point4_stride(L, int(sizeof(TO)));
+    static constexpr int MODE = point4_out_mode(L, int(sizeof(TO)));
 };
 
 template <int L, typename TO>
 __host__ __device__ constexpr size_t point4_warp_bytes(int P) {
-    return align16(size_t(P) * Row4<L>::S * sizeof(TO)) + align16(size_t(3 * P) * Row4<L>::S * sizeof(TO));
+    return align16(size_t(P) * Row4<L, TO>::S * sizeof(TO)) + align16(size_t(3 * P) * Row4<L, TO>::S * sizeof(TO));
+}
+
+// One tile of a set: points [p0, p0 + cnt), cnt <= P <= 8, lane 4j + r
+// computing plane r of point j at (x, y, z); outputs staged at buf
+// (point4_warp_bytes<L, TO>(P) bytes) and sent to the set's sph / dsph.
+// Warp-collective; returns with the staging buffer free for the next tile.
+template <int L, bool NORM, typename T, typename TO, typename Tabs>
+__device__ __forceinline__ void point4_tile(TO* __restrict__ sph, TO* __restrict__ dsph, int64_t p0, int cnt, int P,
+                                            int bulk, unsigned char* buf, const Tabs& tb, int lane, T x, T y, T z) {
+    constexpr int K = (L + 1) * (L + 1);
+    constexpr int S = Row4<L, TO>::S;
+    constexpr int MODE = Row4<L, TO>::MODE;
+    const int pt = lane >> 2, r = lane & 3;
+    TO* s_v = reinterpret_cast<TO*>(buf);
+    TO* s_d = reinterpret_cast<TO*>(buf + align16(size_t(P) * S * sizeof(TO)));
+    TO* rowp = r == 0 ? s_v + size_t(pt) * S : s_d + size_t(3 * pt + r - 1) * S;
+    if (pt < cnt) {
+        T r2, ir = T(1);
+        if (NORM) {
+            unit_point(x, y, z, r2, ir);
+        } else {
+            r2 = x * x + y * y + z * z;
+        }
+        point4_core<L, NORM>(x, y, z, r2, tb, r, ir, rowp);
+    }
+    if constexpr (MODE == 1) {
+        if (bulk) {  // each lane sends the row it wrote (16-byte aligned at both ends)
+            if (pt < cnt) {
+                fence_proxy_async_smem();
+                TO* g = r == 0 ? sph + (p0 + pt) * K : dsph + ((p0 + pt) * 3 + (r - 1)) * K;
+                bulk_store(g, rowp, uint32_t(K * sizeof(TO)));
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+            __syncwarp();
+            return;
+        }
+    }
+    if constexpr (MODE != 0) {
+        __syncwarp();
+        warp_rows_out<K>(sph + p0 * K, s_v, cnt, S, lane);
+        warp_rows_out<K>(dsph + p0 * 3 * K, s_d, 3 * cnt, S, lane);
+        __syncwarp();
+        return;
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t ev = int64_t(cnt) * K;
+    int64_t ev_bulk = 0, ed_bulk = 0;
+    if (bulk) {
+        ev_bulk = (ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
+        ed_bulk = (3 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
+        if (lane == 0) {
+            if (ev_bulk) bulk_store(sph + p0 * K, s_v, uint32_t(ev_bulk * sizeof(TO)));
+            if (ed_bulk) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * sizeof(TO)));
+            bulk_commit();
+        }
+    }
+    for (int64_t i = ev_bulk + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
+    for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
+    if (bulk && lane == 0) bulk_wait_read_all();
+    __syncwarp();
 }
 
 template <int L, bool NORM, typename T, typename TO>
@@ -452,16 +516,12 @@ __global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ x
                                                          const __grid_constant__ PointTabs<L, T, false> tb,
                                                          TO* __restrict__ sph, TO* __restrict__ dsph, int P,
                                                          int bulk) {
-    constexpr int K = (L + 1) * (L + 1);
-    constexpr int S = Row4<L>::S;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
-    const int pt = lane >> 2, r = lane & 3;
-    TO* s_v = reinterpret_cast<TO*>(smem + size_t(warp) * point4_warp_bytes<L, TO>(P));
-    TO* s_d = reinterpret_cast<TO*>(reinterpret_cast<unsigned char*>(s_v) + align16(size_t(P) * S * sizeof(TO)));
-    TO* rowp = r == 0 ? s_v + size_t(pt) * S : s_d + size_t(3 * pt + r - 1) * S;
+    const int pt = lane >> 2;
+    unsigned char* buf = smem + size_t(warp) * point4_warp_bytes<L, TO>(P);
 
     const int64_t ntiles = (n + P - 1) / P;
     const int64_t stride = int64_t(gridDim.x) * W;
@@ -476,7 +536,7 @@ __global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ x
         }
     }
     for (; tile < ntiles; tile += stride) {
-        T x = nx, y = ny, z = nz;
+        const T x = nx, y = ny, z = nz;
         const int64_t nt = tile + stride;
         if (nt < ntiles && pt < P) {
             const int64_t p = nt * P + pt;
@@ -488,41 +548,9 @@ __global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ x
         }
         const int64_t p0 = tile * P;
         const int cnt = int(min(int64_t(P), n - p0));
-        if (pt < cnt) {
-            T r2, ir = T(1);
-            if (NORM) {
-                unit_point(x, y, z, r2, ir);
-            } else {
-                r2 = x * x + y * y + z * z;
-            }
-            point4_core<L, NORM>(x, y, z, r2, tb, r, ir, rowp);
-        }
-        if constexpr (Row4<L>::PAD) {
-            __syncwarp();
-            warp_rows_out<K>(sph + p0 * K, s_v, cnt, S, lane);
-            warp_rows_out<K>(dsph + p0 * 3 * K, s_d, 3 * cnt, S, lane);
-            __syncwarp();
-            continue;
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        const int64_t ev = int64_t(cnt) * K;
-        int64_t ev_bulk = 0, ed_bulk = 0;
-        if (bulk) {
-            ev_bulk = (ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
-            ed_bulk = (3 * ev * int64_t(sizeof(TO))) / 16 * 16 / int64_t(sizeof(TO));
-            if (lane == 0) {
-                if (ev_bulk) bulk_store(sph + p0 * K, s_v, uint32_t(ev_bulk * sizeof(TO)));
-                if (ed_bulk) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_bulk * sizeof(TO)));
-                bulk_commit();
-            }
-        }
-        for (int64_t i = ev_bulk + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
-        for (int64_t i = ed_bulk + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
-        if (bulk && lane == 0) bulk_wait_read_all();
-        __syncwarp();
+        point4_tile<L, NORM>(sph, dsph, p0, cnt, P, bulk, buf, tb, lane, x, y, z);
     }
-    if (bulk && lane == 0) bulk_wait_all();
+    if (bulk) bulk_wait_all();  // every lane: row copies are issued per lane
 }
 
 // ----------------------------------------------------------------- backward

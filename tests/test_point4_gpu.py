@@ -58,7 +58,7 @@ def test_matches_one_lane_point():
 
 def test_bf16_storage_against_oracle():
     x = inputs.shell_points(2000 + 7, 0.5, 2.0, seed=322).astype(np.float32).astype(np.float64)
-    for l_max in (4, 9, 12, 16):
+    for l_max in (4, 9, 11, 12, 13, 15, 16):
         v, g = api.spherical_harmonics(_t(x), l_max, True, gradients=True, kernel="point", launch=_four(),
                                        out_dtype=torch.bfloat16)
         rv, rg = oracle.spherical_harmonics_grad(x, l_max, True)
@@ -85,16 +85,18 @@ def test_output_buffers_bounded():
     """Writes stay inside [n, K] / [n, 3, K] (odd and even K): guard rows
     around the outputs keep their sentinel."""
     n = 77
-    for l_max in (12, 13):
+    for l_max, odt in ((11, torch.float32), (12, torch.float32), (13, torch.float32), (15, torch.float32),
+                       (11, torch.bfloat16), (13, torch.bfloat16)):
         K = (l_max + 1) ** 2
-        big_v = torch.full((n + 2, K), 7.0, device=DEV)
-        big_g = torch.full((n + 2, 3, K), 7.0, device=DEV)
+        big_v = torch.full((n + 2, K), 7.0, device=DEV, dtype=odt)
+        big_g = torch.full((n + 2, 3, K), 7.0, device=DEV, dtype=odt)
         v, g = big_v[1:n + 1], big_g[1:n + 1]
         api.spherical_harmonics(_t(inputs.normal_points(n, seed=324)), l_max, True, gradients=True,
-                                kernel="point", launch=_four(), out=(v, g))
+                                kernel="point", launch=_four(), out=(v, g), out_dtype=odt)
         torch.cuda.synchronize()
         for t in (big_v[0], big_v[-1], big_g[0], big_g[-1]):
-            assert bool((t == 7.0).all()), l_max
+            assert bool((t == 7.0).all()), (l_max, odt)
+        assert bool(torch.isfinite(v.float()).all()) and not bool((g == 7.0).all(dim=2).any()), (l_max, odt)
 
 
 def test_launch_shapes_and_limits():
