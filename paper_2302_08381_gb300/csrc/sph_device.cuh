@@ -58,6 +58,11 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
         : "r"(smem_u32(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// Hint: bring `bytes` of global memory at `gsrc` into L2 (16-byte aligned
+// address, size a multiple of 16; no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gsrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(

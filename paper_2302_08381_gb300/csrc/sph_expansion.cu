@@ -63,10 +63,17 @@ struct ValVis {
 };
 
 constexpr int kExpBatch = 32;  // centres whose CSR offsets a warp holds in registers
+// Radial-row buffers per warp. One buffer, refilled after each chunk's
+// contraction while the next chunk's rows were prefetched into L2, leaves
+// room for 12 resident warps per SM where two buffers (the next chunk's rows
+// loaded into shared memory during the current one) leave 8: measured on
+// GB300, 0.267 against 0.369 ms (l_max 6, 8 radial, 100k centres x ~40
+// points).
+constexpr int kExpRBuf = 1;
 
-// Per-warp shared memory: Y rows of a 32-point chunk (grouped layout), two
-// buffers of the chunk's radial rows in their global layout [e][n][l]
-// (filled by bulk copies one chunk ahead), the [n_rad, K] partial sums of a
+// Per-warp shared memory: Y rows of a 32-point chunk (grouped layout),
+// kExpRBuf buffers of the chunk's radial rows in their global layout
+// [e][n][l] (filled by bulk copies), the [n_rad, K] partial sums of a
 // centre that continues into the next chunk, the chunk's segment table (end
 // of each centre's points within the chunk, and the centre) and two mbarriers.
 template <int L, typename T>
@@ -76,7 +83,7 @@ __host__ __device__ constexpr size_t expansion_warp_bytes(int nr) {
     // radial buffers: 32 rows plus 3 rows' worth of channels that the masked
     // channels of the last row's items read past its end
     return align16(size_t(32) * exp_row_words<L>() * sizeof(T)) +
-           2 * align16((size_t(32) * RW + 3 * (L + 1)) * sizeof(T)) + align16(size_t(nr) * K * sizeof(T)) +
+           kExpRBuf * align16((size_t(32) * RW + 3 * (L + 1)) * sizeof(T)) + align16(size_t(nr) * K * sizeof(T)) +
            align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))) + 16;
 }
 
@@ -169,8 +176,10 @@ __device__ __forceinline__ void zero_malformed(const ExpBatch& bt, T* __restrict
 // chunks of 32 that cross centre boundaries: a chunk's harmonics are computed
 // one point per lane, and each lane accumulates its (column, channel) items
 // over the chunk's segments, writing a centre's sums to global memory from
-// registers when the centre ends. The radial rows and coordinates of the next
-// chunk, and the offsets of the next 32 centres, are loaded one step ahead.
+// registers when the centre ends. The coordinates of the next chunk and the
+// offsets of the next 32 centres are loaded one step ahead; the next chunk's
+// radial rows are prefetched into L2 during the current chunk and copied into
+// the (single) shared-memory buffer once its contraction is done.
 template <int L, bool NORM, typename T>
 __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xyz, const T* __restrict__ R,
                                                         const int64_t* __restrict__ offsets, int64_t ncent,
@@ -191,11 +200,11 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
     const size_t cbytes = align16(size_t(nr) * K * sizeof(T));
     T* Ys = reinterpret_cast<T*>(base);
     T* Rb0 = reinterpret_cast<T*>(base + ybytes);
-    T* Rb1 = reinterpret_cast<T*>(base + ybytes + rbytes);
-    T* Cs = reinterpret_cast<T*>(base + ybytes + 2 * rbytes);
-    int64_t* seg_cid = reinterpret_cast<int64_t*>(base + ybytes + 2 * rbytes + cbytes);
+    T* Rb1 = reinterpret_cast<T*>(base + ybytes + (kExpRBuf - 1) * rbytes);
+    T* Cs = reinterpret_cast<T*>(base + ybytes + kExpRBuf * rbytes);
+    int64_t* seg_cid = reinterpret_cast<int64_t*>(base + ybytes + kExpRBuf * rbytes + cbytes);
     int* seg_end = reinterpret_cast<int*>(seg_cid + kExpBatch);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + 2 * rbytes + cbytes +
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + ybytes + kExpRBuf * rbytes + cbytes +
                                                 align16(size_t(kExpBatch) * (sizeof(int64_t) + sizeof(int))));
     const int nout = nr * K;
     const int NG = (nr + 3) / 4;  // radial channel groups of 4
@@ -272,10 +281,14 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
         const int64_t p0 = ch.p;
         // the next chunk: its radial rows and coordinates are loaded during this one
         const ExpChunk nch = next_chunk(after_chunk(ch));
-        const int nb = b ^ 1;
+        const int nb = kExpRBuf == 2 ? (b ^ 1) : 0;
         T nxx = T(0), nxy = T(0), nxz = T(0);
         if (nch.valid && !failed) {
-            issue(nb, nch);
+            if constexpr (kExpRBuf == 2) {
+                issue(nb, nch);
+            } else if (bulk && lane == 0 && nch.cnt > 0) {
+                bulk_prefetch_l2(R + nch.p * RW, uint32_t(size_t(nch.cnt) * RW * sizeof(T)));
+            }
             coords(nch, nxx, nxy, nxz);
         }
         // harmonics of this chunk, one point per lane
@@ -398,6 +411,7 @@ __global__ void __launch_bounds__(256) expansion_kernel(const T* __restrict__ xy
         }
         fence_proxy_async_smem();  // generic reads of Rs done before the buffer is refilled
         __syncwarp();
+        if (kExpRBuf == 1 && nch.valid && !failed) issue(0, nch);  // refill the one buffer
         ch = nch;
         b = nb;
         px = nxx;
