@@ -125,11 +125,14 @@ typedef enum {
  *   points_per_tile  points a warp computes per tile, 4..32, multiple of 4
  *   warps_per_block  independent warps per CTA, 1..8
  *   blocks_per_sm    resident CTAs per SM to size the persistent grid (0 = max)
- *   lanes_per_point  POINT: 0 (default), 1, or 4 = one lane per output plane
+ *   lanes_per_point  POINT: 0 (default), 1, 4 = one lane per output plane
  *                    (value, d/dx, d/dy, d/dz) of each point, points_per_tile
  *                    <= 8: every lane busy where one-lane tiles that fit
  *                    shared memory are short (FP32 arithmetic, gradients, no
- *                    Hessians); SLICE: 8, 16 or 32 (0 = by l_max)
+ *                    Hessians), or 16 = one lane per plane of the value,
+ *                    gradient and 3x3 Hessian (FP32 Hessians, FP32 storage;
+ *                    points_per_tile even and <= 8, warps_per_block <= 4);
+ *                    SLICE: 8, 16 or 32 (0 = by l_max)
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
  * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
@@ -137,7 +140,9 @@ typedef enum {
  * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
  * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
  * the FP64 pipe), and with FP32 gradients from l_max 10 runs 4 lanes per
- * point on 8-point tiles; when a call has fewer than 2 x SMs x
+ * point on 8-point tiles, with FP32 Hessians 16 lanes per point where that
+ * measured faster (scaled l_max 8..10, normalized from l_max 9); when a call
+ * has fewer than 2 x SMs x
  * warps_per_block tiles, it runs fewer warps per block so that the blocks
  * reach every SM.                                                           */
 typedef struct {

@@ -575,10 +575,8 @@ constexpr size_t kNoAllocScratchBytes = sizeof(sph_batch_set) * kNoAllocMaxSets;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;                            // guards the two arrays below
-void* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};   // device address of g_noalloc_scratch, per device
-sph_batch_set g_noalloc_host[kNoAllocMaxSets];      // host staging of the descriptors
+std::mutex g_noalloc_mu;                        // guards the staging array below
+sph_batch_set g_noalloc_host[kNoAllocMaxSets];  // host staging of the descriptors
 
 }  // namespace
 }  // namespace sph
@@ -631,26 +629,24 @@ extern "C" int sphericart_batch_compute_noalloc(const sph_batch_set* sets, int n
         }
     }
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         set_error("batch_compute_noalloc: no usable CUDA device");
         return SPH_ECUDA;
     }
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    // Set-up, once per device, with that device current: the device address
-    // of the static array (host code must not use the symbol itself).
-    if (!g_noalloc_dev_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            set_error("batch_compute_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return SPH_ECUDA;
-        }
-        g_noalloc_dev_ptr[dev] = p;
+    // The current device's address of the static array, looked up on every
+    // call (host code must not use the symbol itself; a cached address would
+    // not survive a device reset or a new primary context).
+    void* p = nullptr;
+    const cudaError_t es = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (es != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_error("batch_compute_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(es));
+        return SPH_ECUDA;
     }
-    sph_batch_set* d_sets = static_cast<sph_batch_set*>(g_noalloc_dev_ptr[dev]);
+    sph_batch_set* d_sets = static_cast<sph_batch_set*>(p);
 
     // Descriptors grouped by flag class (gradients, normalized), stable.
     int count[5] = {0, 0, 0, 0, 0};

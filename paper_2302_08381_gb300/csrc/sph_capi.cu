@@ -287,6 +287,29 @@ sph_launch default_point4_fwd(int L, int elem) {
     return sph_launch{8, point4_default_warps(L), 16, 4};
 }
 
+// Shared-memory bytes per point of the 16-lanes-per-point Hessian tile (FP32):
+// 13 rows of stride point4_stride.
+size_t point16_row_bytes(int L) { return size_t(4) * 13 * size_t(point4_stride(L, 4)); }
+
+// Default shape of the 16-lanes-per-point Hessian tile: 4 points per warp (two
+// passes of two points), as many blocks as fit; 4-warp blocks while three of
+// them fit on an SM (l_max <= 8), else one-warp blocks (measured on GB300:
+// with larger tiles a 4-warp block leaves the SM at 4 resident warps).
+sph_launch default_point16_fwd(int L) {
+    const size_t tile = 4 * point16_row_bytes(L) + 64;
+    const int W = 3 * 4 * tile <= size_t(max_smem_optin()) ? 4 : 1;
+    return sph_launch{4, W, 0, 16};
+}
+
+// Whether the POINT default runs FP32 Hessians on 16 lanes per point.
+// Measured on GB300 (1M / 400k / 200k points, l_max 4..16): faster for the
+// scaled form at l_max 8..10 (+6..10 %) and for the normalized form from
+// l_max 9 (1.4..2.3x at l_max 10..16); the one-lane tile is faster elsewhere.
+bool point16_default(int L, int hess, int normalized, int dtype, int out) {
+    if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME) return false;
+    return normalized ? L >= 9 : (L >= 8 && L <= 10);
+}
+
 // Whether the POINT default (no shape given, none tuned) runs 4 lanes per
 // point: FP32 arithmetic with gradients, no Hessians, l_max >= 10 (where the
 // one-lane tile that fits shared memory leaves most lanes idle).
@@ -572,24 +595,38 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
         }
         const int hess = ddsph ? 1 : 0;
         if (from_default && a.launch.points_per_tile == 0 && a.launch.warps_per_block == 0 &&
-            a.launch.blocks_per_sm == 0 && a.launch.lanes_per_point == 0 &&
-            point4_default(l_max, grad, eo, hess, hc))
-            a.launch.lanes_per_point = 4;
+            a.launch.blocks_per_sm == 0 && a.launch.lanes_per_point == 0) {
+            if (point4_default(l_max, grad, eo, hess, hc))
+                a.launch.lanes_per_point = 4;
+            else if (point16_default(l_max, hess, normalized, dtype, out))
+                a.launch.lanes_per_point = 16;
+        }
         const int lpp = a.launch.lanes_per_point;
-        if (lpp != 0 && lpp != 1 && lpp != 4) {
-            set_error("POINT launch: lanes_per_point must be 0, 1 or 4");
+        if (lpp != 0 && lpp != 1 && lpp != 4 && lpp != 16) {
+            set_error("POINT launch: lanes_per_point must be 0, 1, 4 or 16");
             return SPH_EINVAL;
         }
         if (lpp == 4 && (!grad || hess || dtype != SPH_F32 || hc)) {
             set_error("POINT with 4 lanes per point takes FP32 arithmetic, values and gradients (no Hessians)");
             return SPH_EUNSUPPORTED;
         }
-        const sph_launch dflt = lpp == 4 ? default_point4_fwd(l_max, eo) : default_point_fwd(l_max, grad, eo, hess);
-        if (!resolve_point(a.launch, dflt, l_max, eo,
-                           lpp == 4 ? point4_row_bytes(l_max, eo) : point_row_bytes(l_max, grad, eo, hess)))
-            return SPH_EINVAL;
+        if (lpp == 16 && (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME || hc)) {
+            set_error("POINT with 16 lanes per point takes FP32 arithmetic and storage with Hessians");
+            return SPH_EUNSUPPORTED;
+        }
+        const sph_launch dflt = lpp == 4    ? default_point4_fwd(l_max, eo)
+                                : lpp == 16 ? default_point16_fwd(l_max)
+                                            : default_point_fwd(l_max, grad, eo, hess);
+        const size_t row = lpp == 4 ? point4_row_bytes(l_max, eo)
+                           : lpp == 16 ? point16_row_bytes(l_max)
+                                       : point_row_bytes(l_max, grad, eo, hess);
+        if (!resolve_point(a.launch, dflt, l_max, eo, row)) return SPH_EINVAL;
         if (lpp == 4 && a.launch.points_per_tile > 8) {
             set_error("POINT with 4 lanes per point: points_per_tile must be <= 8 (32 lanes per warp)");
+            return SPH_EINVAL;
+        }
+        if (lpp == 16 && (a.launch.points_per_tile > 8 || a.launch.points_per_tile % 2 || a.launch.warps_per_block > 4)) {
+            set_error("POINT with 16 lanes per point: points_per_tile even and <= 8, warps_per_block <= 4");
             return SPH_EINVAL;
         }
         if (from_default) {
@@ -806,12 +843,16 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
             auto it = g_tuned.find(TuneKey{d, l_max, dtype, out, hess ? 2 : (grad ? 1 : 0)});
             if (it != g_tuned.end()) s = it->second;
         }
-        const bool four = s.lanes_per_point == 4 ||
-                          (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0 &&
-                           s.lanes_per_point == 0 && point4_default(l_max, grad, eo, hess, hc ? 1 : 0));
-        const sph_launch dflt =
-            four ? default_point4_fwd(l_max, eo) : default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
+        const bool none = s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0 &&
+                          s.lanes_per_point == 0;
+        const bool four = s.lanes_per_point == 4 || (none && point4_default(l_max, grad, eo, hess, hc ? 1 : 0));
+        // (the scaled form's choice: launch_info takes no normalized flag)
+        const bool sixteen = s.lanes_per_point == 16 || (none && !four && point16_default(l_max, hess, 0, dtype, out));
+        const sph_launch dflt = four      ? default_point4_fwd(l_max, eo)
+                                : sixteen ? default_point16_fwd(l_max)
+                                          : default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
         if (four) s.lanes_per_point = 4;
+        if (sixteen) s.lanes_per_point = 16;
         // as resolve_point: no tuned shape at all takes the whole default
         if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = dflt.blocks_per_sm;
         if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;

@@ -553,6 +553,279 @@ __global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ x
     if (bulk) bulk_wait_all();  // every lane: row copies are issued per lane
 }
 
+// ------------------------- forward with Hessians, 16 lanes per point (planes)
+// POINT with lanes_per_point = 16 (FP32 values, gradients and Hessians):
+// lane 16j + r owns output plane r of point j of the current pair of points
+// (0 the value, 1..3 the gradient, 4..12 the Hessian entries (i, k) row-major;
+// lanes 13..15 compute plane 12 again and store nothing). Every lane runs the
+// recursions in full and assembles its plane from one instance of the terms
+// of Eq. iter-deri applied once and twice:
+//   plane = A C + m B T1 + m (m - 1) Qtilde_l^m T2
+//   A = aQ Qtilde + aE e Qtilde_{l-1}^{m+1} + az f Qtilde_{l-1}^m
+//       + a2 g2 Qtilde_{l-2}^{m+2} + a3 g3 Qtilde_{l-2}^{m+1} + a4 g4 Qtilde_{l-2}^m
+//   B = bQ Qtilde + bE e Qtilde_{l-1}^{m+1} + bz f Qtilde_{l-1}^m
+// with C = c_m (or s_m for the sin-type column), T1 a role combination of
+// c_{m-1}, s_{m-1} and T2 of c_{m-2}, s_{m-2} (the derivatives of c_m, s_m),
+// role weights from the point's coordinates. The normalized form needs the
+// value and two gradient components of the same column: taken from the
+// point's lanes 0 and 1 + i by warp shuffles.
+template <int L, bool NORM, typename Tabs>
+__device__ __forceinline__ void point16_core(float x, float y, float z, float r2, const Tabs& tb, int lane,
+                                             float ir, float* __restrict__ rowp) {
+    const int r = lane & 15;
+    const int rr = r < 13 ? r : 12;
+    const int hi = rr >= 4 ? (rr - 4) / 3 : 0, hk = rr >= 4 ? (rr - 4) % 3 : 0;
+    // the symmetric entry (i, k) with i <= k selects the formula
+    const int i0 = hi < hk ? hi : hk, k0 = hi < hk ? hk : hi;
+    const bool isv = rr == 0, isgx = rr == 1, isgy = rr == 2, isgz = rr == 3, ish = rr >= 4;
+    const bool hxx = ish && i0 == 0 && k0 == 0, hxy = ish && i0 == 0 && k0 == 1, hxz = ish && i0 == 0 && k0 == 2;
+    const bool hyy = ish && i0 == 1 && k0 == 1, hyz = ish && i0 == 1 && k0 == 2, hzz = ish && i0 == 2 && k0 == 2;
+    const float X = x, Y = y;
+    const float aQ = isv ? 1.f : 0.f;
+    const float aE = isgx ? X : (isgy ? Y : ((hxx || hyy) ? 1.f : 0.f));
+    const float az = isgz ? 1.f : 0.f;
+    const float a2 = hxx ? X * X : (hyy ? Y * Y : (hxy ? X * Y : 0.f));
+    const float a3 = hxz ? X : (hyz ? Y : 0.f);
+    const float a4 = hzz ? 1.f : 0.f;
+    const float bQ = (isgx || isgy) ? 1.f : 0.f;
+    const float bE = (hxx || hyy || hxy) ? 1.f : 0.f;
+    const float bz = (hxz || hyz) ? 1.f : 0.f;
+    // T1c = k1c c1 + k1s s1, T1s = k2c c1 + k2s s1, T2c = k3c c2 + k3s s2, T2s = k4c c2 + k4s s2
+    float k1c = 0.f, k1s = 0.f, k2c = 0.f, k2s = 0.f, k3c = 0.f, k3s = 0.f, k4c = 0.f, k4s = 0.f;
+    if (isgx || hxz) {
+        k1c = 1.f;
+        k2s = 1.f;
+    } else if (isgy || hyz) {
+        k1s = -1.f;
+        k2c = 1.f;
+    } else if (hxx) {
+        k1c = 2.f * X;
+        k2s = 2.f * X;
+        k3c = 1.f;
+        k4s = 1.f;
+    } else if (hyy) {
+        k1s = -2.f * Y;
+        k2c = 2.f * Y;
+        k3c = -1.f;
+        k4s = -1.f;
+    } else if (hxy) {
+        k1c = Y;
+        k1s = -X;
+        k2c = X;
+        k2s = Y;
+        k3s = -1.f;
+        k4c = 1.f;
+    }
+    float c[L + 1], s[L + 1];
+    point_cs<L>(x, y, c, s);
+    // Normalized form: plane' = sc (plane + wv v + wi g_i + wk g_k), v and g from
+    // the point's lanes 0 and 1 + i / 1 + k (raw values at the unit point).
+    // (i0, k0) for both (i, k) and (k, i): the two planes of a symmetric pair
+    // run the same operations and come out bit-identical
+    const int base = lane & 16;
+    const int src_i = base + 1 + i0, src_k = base + 1 + k0;
+    const float ui = i0 == 0 ? x : (i0 == 1 ? y : z), uk = k0 == 0 ? x : (k0 == 1 ? y : z);
+    const float ug = isgx ? x : (isgy ? y : z);  // gradient planes: u of their component
+    const float sc = !NORM || isv ? 1.f : (ish ? ir * ir : ir);
+    float q1[L + 1], q2[L + 1];
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        q1[m] = 0.f;
+        q2[m] = 0.f;
+    }
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+        float q[L + 1];
+        q[l] = tb.qll[l];
+        if (l >= 1) q[l - 1] = tb.d[l] * z * q1[l - 1];
+#pragma unroll
+        for (int m = 0; m + 2 <= l; ++m) {  // Eq. iter-q, folded
+            const int i = tri(l, m);
+            q[m] = (tb.a[i] * z) * q1[m] - (tb.b[i] * r2) * q2[m];
+        }
+        const float lf = float(l);
+        // normalization weights of this degree
+        float wv = 0.f, wi = 0.f, wk = 0.f;
+        if (NORM) {
+            if (ish) {
+                wv = lf * (lf + 2.f) * ui * uk - (i0 == k0 ? lf : 0.f);
+                wi = -lf * uk;
+                wk = -lf * ui;
+            } else if (!isv) {
+                wv = -lf * ug;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            const int i = tri(l, m);
+            const float E1 = (m + 1 <= l - 1) ? tb.e[i] * q1[m + 1] : 0.f;
+            const float Qz = (m <= l - 1) ? tb.fz[i] * q1[m] : 0.f;
+            const float G2 = (m + 2 <= l - 2) ? tb.g2[i] * q2[m + 2] : 0.f;
+            const float G3 = (m + 1 <= l - 2) ? tb.g3[i] * q2[m + 1] : 0.f;
+            const float G4 = (m <= l - 2) ? tb.g4[i] * q2[m] : 0.f;
+            const float A = aE * E1 + az * Qz + a2 * G2 + a3 * G3 + a4 * G4;
+            if (m == 0) {
+                float out = aQ * tb.inv_sqrt2 * q[0] + A;
+                if (NORM) {
+                    const float v = __shfl_sync(0xffffffffu, out, base);
+                    const float gi = __shfl_sync(0xffffffffu, out, src_i);
+                    const float gk = __shfl_sync(0xffffffffu, out, src_k);
+                    out = sc * (out + wv * v + wi * gi + wk * gk);
+                }
+                if (r < 13) rowp[l * l + l] = out;
+            } else {
+                const float Am = aQ * q[m] + A;
+                const float mB = float(m) * (bQ * q[m] + bE * E1 + bz * Qz);
+                const float MQ = float(m * (m - 1)) * q[m];
+                const float c1 = c[m - 1], s1 = s[m - 1];
+                const float c2 = m >= 2 ? c[m >= 2 ? m - 2 : 0] : 0.f, s2 = m >= 2 ? s[m >= 2 ? m - 2 : 0] : 0.f;
+                float oc = Am * c[m] + mB * (k1c * c1 + k1s * s1);
+                float os = Am * s[m] + mB * (k2c * c1 + k2s * s1);
+                if (m >= 2) {
+                    oc += MQ * (k3c * c2 + k3s * s2);
+                    os += MQ * (k4c * c2 + k4s * s2);
+                }
+                if (NORM) {
+                    const float vc = __shfl_sync(0xffffffffu, oc, base);
+                    const float gic = __shfl_sync(0xffffffffu, oc, src_i);
+                    const float gkc = __shfl_sync(0xffffffffu, oc, src_k);
+                    const float vs = __shfl_sync(0xffffffffu, os, base);
+                    const float gis = __shfl_sync(0xffffffffu, os, src_i);
+                    const float gks = __shfl_sync(0xffffffffu, os, src_k);
+                    oc = sc * (oc + wv * vc + wi * gic + wk * gkc);
+                    os = sc * (os + wv * vs + wi * gis + wk * gks);
+                }
+                if (r < 13) {
+                    rowp[l * l + l + m] = oc;
+                    rowp[l * l + l - m] = os;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            q2[m] = q1[m];
+            q1[m] = q[m];
+        }
+    }
+}
+
+// Shared-memory bytes of a 16-lane Hessian tile of P points: value rows,
+// gradient rows and Hessian rows, each part 16-byte aligned, stride
+// point4_stride (the same rules as the 4-lane tile).
+template <int L>
+__host__ __device__ constexpr size_t point16_warp_bytes(int P) {
+    constexpr size_t S = size_t(point4_stride(L, 4)) * 4;
+    return align16(size_t(P) * S) + align16(size_t(3 * P) * S) + align16(size_t(9 * P) * S);
+}
+
+constexpr int kPoint16MaxTile = 8;  // points per tile (pairs of points per pass)
+
+// One tile of P <= 8 points (P even): the warp computes two points per pass,
+// 16 lanes each, into the staged image; warp-collective.
+template <int L, bool NORM, typename Tabs>
+__device__ __forceinline__ void point16_tile(const float* __restrict__ xyz, float* __restrict__ sph,
+                                             float* __restrict__ dsph, float* __restrict__ ddsph, int64_t p0,
+                                             int cnt, int P, int bulk, unsigned char* buf, const Tabs& tb,
+                                             int lane) {
+    constexpr int K = (L + 1) * (L + 1);
+    constexpr int S = point4_stride(L, 4);
+    constexpr int MODE = point4_out_mode(L, 4);
+    float* s_v = reinterpret_cast<float*>(buf);
+    float* s_d = reinterpret_cast<float*>(buf + align16(size_t(P) * S * 4));
+    float* s_h = reinterpret_cast<float*>(buf + align16(size_t(P) * S * 4) + align16(size_t(3 * P) * S * 4));
+    const int r = lane & 15, half = lane >> 4;
+    // coordinates of every pass of the tile, loaded up front
+    float cx[kPoint16MaxTile / 2], cy[kPoint16MaxTile / 2], cz[kPoint16MaxTile / 2];
+#pragma unroll
+    for (int t = 0; t < kPoint16MaxTile / 2; ++t) {
+        const int j = 2 * t + half;
+        cx[t] = 0.f;
+        cy[t] = 0.f;
+        cz[t] = 1.f;  // points past the end run on a unit vector and are not sent
+        if (2 * t < P && j < cnt) {
+            cx[t] = xyz[3 * (p0 + j)];
+            cy[t] = xyz[3 * (p0 + j) + 1];
+            cz[t] = xyz[3 * (p0 + j) + 2];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kPoint16MaxTile / 2; ++t) {
+        if (2 * t >= P) break;
+        const int j = 2 * t + half;
+        float x = cx[t], y = cy[t], z = cz[t], r2, ir = 1.f;
+        if (NORM) {
+            unit_point(x, y, z, r2, ir);
+        } else {
+            r2 = x * x + y * y + z * z;
+        }
+        const int rr = r < 13 ? r : 12;
+        float* rowp = rr == 0 ? s_v + size_t(j) * S
+                              : (rr < 4 ? s_d + size_t(3 * j + rr - 1) * S : s_h + size_t(9 * j + rr - 4) * S);
+        point16_core<L, NORM>(x, y, z, r2, tb, lane, ir, rowp);
+        if constexpr (MODE == 1) {
+            if (bulk && r < 13 && j < cnt) {  // each lane sends the row it wrote
+                fence_proxy_async_smem();
+                float* g = rr == 0 ? sph + (p0 + j) * K
+                                   : (rr < 4 ? dsph + ((p0 + j) * 3 + rr - 1) * K : ddsph + ((p0 + j) * 9 + rr - 4) * K);
+                bulk_store(g, rowp, uint32_t(K * 4));
+                bulk_commit();
+            }
+        }
+    }
+    if constexpr (MODE == 1) {
+        if (bulk) {
+            bulk_wait_read_all();
+            __syncwarp();
+            return;
+        }
+    }
+    if (MODE != 0 || !bulk) {
+        __syncwarp();
+        warp_rows_out<K>(sph + p0 * K, s_v, cnt, S, lane);
+        warp_rows_out<K>(dsph + p0 * 3 * K, s_d, 3 * cnt, S, lane);
+        warp_rows_out<K>(ddsph + p0 * 9 * K, s_h, 9 * cnt, S, lane);
+        __syncwarp();
+        return;
+    }
+    // MODE 0 with bulk copies: the image of the three global ranges; the tile
+    // start is 16-byte aligned (P is a multiple of the tile multiple)
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t ev = int64_t(cnt) * K;
+    const int64_t ev_b = (ev * 4) / 16 * 4, ed_b = (3 * ev * 4) / 16 * 4, eh_b = (9 * ev * 4) / 16 * 4;
+    if (lane == 0) {
+        if (ev_b) bulk_store(sph + p0 * K, s_v, uint32_t(ev_b * 4));
+        if (ed_b) bulk_store(dsph + p0 * 3 * K, s_d, uint32_t(ed_b * 4));
+        if (eh_b) bulk_store(ddsph + p0 * 9 * K, s_h, uint32_t(eh_b * 4));
+        bulk_commit();
+    }
+    for (int64_t i = ev_b + lane; i < ev; i += 32) sph[p0 * K + i] = s_v[i];
+    for (int64_t i = ed_b + lane; i < 3 * ev; i += 32) dsph[p0 * 3 * K + i] = s_d[i];
+    for (int64_t i = eh_b + lane; i < 9 * ev; i += 32) ddsph[p0 * 9 * K + i] = s_h[i];
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+}
+
+template <int L, bool NORM>
+__global__ void __launch_bounds__(128, 3) point16_fwd_kernel(const float* __restrict__ xyz, int64_t n,
+                                                          const __grid_constant__ PointTabs<L, float, true> tb,
+                                                          float* __restrict__ sph, float* __restrict__ dsph,
+                                                          float* __restrict__ ddsph, int P, int bulk) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    unsigned char* buf = smem + size_t(warp) * point16_warp_bytes<L>(P);
+    const int64_t ntiles = (n + P - 1) / P;
+    const int64_t stride = int64_t(gridDim.x) * W;
+    for (int64_t tile = int64_t(blockIdx.x) * W + warp; tile < ntiles; tile += stride) {
+        const int64_t p0 = tile * P;
+        const int cnt = int(min(int64_t(P), n - p0));
+        point16_tile<L, NORM>(xyz, sph, dsph, ddsph, p0, cnt, P, bulk, buf, tb, lane);
+    }
+    if (bulk) bulk_wait_all();  // every lane: rows may leave by per-lane copies
+}
+
 // ----------------------------------------------------------------- backward
 // Loads the [cnt, K] tile of `src` at element offset `off` into `dst`: the
 // 16-byte-multiple prefix by a bulk copy on `bar` (if `bulk`), the rest with
@@ -875,6 +1148,26 @@ int launch_point4_fwd(const FwdArgs& a) {
     const bool bulk = (reinterpret_cast<uintptr_t>(a.sph) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0);
     kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
         static_cast<const T*>(a.xyz), a.n, tb, static_cast<TO*>(a.sph), static_cast<TO*>(a.dsph), P, bulk ? 1 : 0);
+    return int(cudaGetLastError());
+}
+
+// POINT forward with Hessians, 16 lanes per point (FP32); P (even, <= 8) and
+// W resolved by the caller.
+template <int L, bool NORM>
+int launch_point16_fwd(const FwdArgs& a) {
+    static const PointTabs<L, float, true> tb = make_point_tabs<L, float, true>();
+    const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
+    const size_t smem = size_t(W) * point16_warp_bytes<L>(P);
+    auto kern = point16_fwd_kernel<L, NORM>;
+    cudaError_t err = ensure_smem(kern, smem);
+    if (err != cudaSuccess) return int(err);
+    const int64_t ntiles = ceil_div(a.n, P);
+    const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
+    const bool bulk = reinterpret_cast<uintptr_t>(a.sph) % 16 == 0 && reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(a.ddsph) % 16 == 0;
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const float*>(a.xyz), a.n, tb, static_cast<float*>(a.sph), static_cast<float*>(a.dsph),
+        static_cast<float*>(a.ddsph), P, bulk ? 1 : 0);
     return int(cudaGetLastError());
 }
 
