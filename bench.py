@@ -768,6 +768,7 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (1_048_576, 8, "l8_grad_hess_f32_one_lane",
          dict(gradients=True, hessians=True, kernel="point", launch=(12, 2, 16, 1)), 4, 13),
         (400_000, 12, "l12_grad_hess_f32_norm_n400k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
+        (100_000, 20, "l20_grad_hess_f32_norm_n100k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
         (400_000, 12, "l12_grad_hess_f32_norm_n400k_one_lane",
          dict(gradients=True, hessians=True, normalized=True, kernel="point", launch=(4, 1, 0, 1)), 4, 13),
         (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
