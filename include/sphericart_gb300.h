@@ -80,8 +80,8 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 /* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
  * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 12); else
  * POINT when l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for
- * FP32 arithmetic without Hessians up to l_max 63; else DEGREE for bfloat16
- * storage without Hessians; else SLICE.
+ * FP32 arithmetic up to l_max 63 (with Hessians: FP32 storage); else DEGREE
+ * for bfloat16 storage without Hessians; else SLICE.
  *   POINT:  one thread per point, the whole (l, m) recursion unrolled in
  *           registers for a compile-time l_max, outputs staged in shared memory
  *           and written with bulk (TMA) copies.
@@ -96,13 +96,14 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
  *           recursion of Eq. iter-q-alt (its printed overall sign corrected:
  *           Q_l^m = -[2(m+1) z Q_l^{m+1} + (x^2+y^2) Q_l^{m+2}]/((l+m+1)(l-m)))
  *           from the tabulated Q_l^l; the paper's one-degree-at-a-time form.
- *   ROW:    FP32 arithmetic, 16 <= l_max <= 63, values and gradients: 8 lanes
- *           per point (lane j owns the channels m = j mod 8, recursion state in
- *           registers, degree l uniform across the lanes); each point's output
- *           rows are staged in shared memory in windows of whole degrees and
- *           written with TMA bulk copies of 32-byte-aligned runs (~1 KB and
- *           longer, which GB300's HBM needs for full write bandwidth). Also a
- *           fused backward (sphericart_backward).
+ *   ROW:    FP32 arithmetic, 16 <= l_max <= 63, values, gradients and
+ *           Hessians (FP32 storage): 8 lanes per point (lane j owns the
+ *           channels m = j mod 8, recursion state in registers, degree l
+ *           uniform across the lanes); each point's output rows are staged in
+ *           shared memory in windows of whole degrees and written with TMA
+ *           bulk copies of 32-byte-aligned runs (~1 KB and longer, which
+ *           GB300's HBM needs for full write bandwidth; 136-column windows with
+ *           Hessians). Also a fused backward (sphericart_backward).
  *   POINT_HC: POINT with the degrees l <= min(l_max, 3) from generated
  *           straight-line ("hard-coded") expressions and Eq. iter-q above
  *           them, as the paper's GPU kernel does (Section 3.2; the hybrid of
@@ -136,7 +137,10 @@ typedef enum {
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
  * by measurement; DEGREE_DOWN takes 1). ROW kernels read warps_per_block
- * (forward 0..2, backward 0..8; 0 = 1 forward, 2 backward) and blocks_per_sm.
+ * (forward 0..2, backward 0..8; 0 = 1 forward, 2 with Hessians and backward),
+ * blocks_per_sm, and lanes_per_point as the forward window policy (0 = by
+ * l_max, 1, 2; with Hessians 0/2 = 136 columns, 1 = one degree of l_max,
+ * 3 = 256 columns).
  * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
  * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
  * the FP64 pipe), and with FP32 gradients from l_max 10 runs 4 lanes per

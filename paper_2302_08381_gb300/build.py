@@ -55,7 +55,7 @@ def _units():
         units.append(("sph_row.cu", f"sph_row_{part}.o", [f"-DSPH_ROW_PART={part}"]))
     for gn in range(4):
         units.append(("sph_batch_one.cu", f"sph_batch_one_gn{gn}.o", [f"-DSPH_BATCH_GN={gn}"]))
-    for src in ("sph_slice.cu", "sph_capi.cu", "sph_batch.cu", "sph_tune.cu", "sph_expansion.cu", "sph_e3nn.cu", "sph_host.cu", "sph_tables.cpp", "sph_point_registry.cpp"):
+    for src in ("sph_row_hess.cu", "sph_slice.cu", "sph_capi.cu", "sph_batch.cu", "sph_tune.cu", "sph_expansion.cu", "sph_e3nn.cu", "sph_host.cu", "sph_tables.cpp", "sph_point_registry.cpp"):
         units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units
 

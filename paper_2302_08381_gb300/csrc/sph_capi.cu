@@ -171,9 +171,10 @@ const void* device_row_tables() {
     if (slots[d]) return slots[d];
     const HostTables& h = host_tables();
     constexpr int kEntries = kRowLanes * kRowDegrees * kRowSlots;
-    std::vector<float> host(size_t(kEntries) * 5, 0.f);
+    std::vector<float> host(size_t(kEntries) * 9, 0.f);
     float* a4 = host.data();
     float* f1 = host.data() + size_t(kEntries) * 4;
+    float* g4 = host.data() + size_t(kEntries) * 5;  // {g2, g3, g4, 0} (the ROW Hessian kernel)
     for (int j = 0; j < kRowLanes; ++j)
         for (int l = 0; l < kRowDegrees; ++l)
             for (int k = 0; k < kRowSlots; ++k) {
@@ -187,6 +188,9 @@ const void* device_row_tables() {
                 a4[4 * o + 2] = float(m == l ? h.qll[i] : 0.0);
                 a4[4 * o + 3] = float(h.e[i] * unfold);
                 f1[o] = float(h.fz[i] * unfold);
+                g4[4 * o + 0] = float(h.g2[i] * unfold);
+                g4[4 * o + 1] = float(h.g3[i] * unfold);
+                g4[4 * o + 2] = float(h.g4[i] * unfold);
             }
     void* p = nullptr;
     if (cudaMalloc(&p, host.size() * sizeof(float)) != cudaSuccess) {
@@ -430,13 +434,14 @@ namespace {
 // in FP64 up to l_max ~ 10; beyond that FP64 arithmetic (FP64 inputs or the
 // mixed mode) is bound by GB300's FP64 pipe, where the DEGREE family (no idle
 // lanes) is fastest; beyond POINT's range FP32 arithmetic runs on ROW up to
-// its l_max 63 (1.8-2.2x SLICE), then on SLICE (DEGREE for bf16 storage);
-// Hessians stay on POINT / SLICE.
+// its l_max 63 (1.8-2.2x SLICE; FP32 Hessians 1.2-1.7x), then on SLICE
+// (DEGREE for bf16 storage).
 int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
     if (!hess && (mixed || (dtype == SPH_F64 && l_max >= 12))) return SPH_KERNEL_DEGREE;
     if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
     if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
+    if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && dtype == SPH_F32 && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && out == SPH_OUT_BF16) return SPH_KERNEL_DEGREE;
     return SPH_KERNEL_SLICE;
@@ -553,8 +558,9 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
         set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
-    if (fam == SPH_KERNEL_ROW && (ddsph || mixed || dtype != SPH_F32 || l_max < kRowMinL || l_max > kRowMaxL)) {
-        set_error("ROW kernels take FP32 arithmetic, %d <= l_max <= %d, values and gradients only", kRowMinL,
+    if (fam == SPH_KERNEL_ROW && (mixed || dtype != SPH_F32 || l_max < kRowMinL || l_max > kRowMaxL ||
+                                  (ddsph && out != SPH_OUT_SAME))) {
+        set_error("ROW kernels take FP32 arithmetic, %d <= l_max <= %d (Hessians with FP32 storage)", kRowMinL,
                   kRowMaxL);
         return SPH_EUNSUPPORTED;
     }
@@ -679,16 +685,16 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             set_error("ROW launch: warps_per_block must be in [0,8] and blocks_per_sm in [0,32]");
             return SPH_EINVAL;
         }
-        if (a.launch.lanes_per_point < 0 || a.launch.lanes_per_point > 2) {
-            set_error("ROW launch: lanes_per_point selects the window policy: 0 (by l_max), 1 or 2");
+        if (a.launch.lanes_per_point < 0 || a.launch.lanes_per_point > (ddsph ? 3 : 2)) {
+            set_error("ROW launch: lanes_per_point selects the window policy: 0 (by l_max), 1 or 2 (Hessians: 0..3)");
             return SPH_EINVAL;
         }
-        const int e = (l_max + 1 + 7) / 8 <= 5 ? row_fwd_part0(a) : row_fwd_part1(a);
+        const int e = ddsph ? row_hess_fwd(a) : ((l_max + 1 + 7) / 8 <= 5 ? row_fwd_part0(a) : row_fwd_part1(a));
         if (e == int(cudaErrorInvalidConfiguration)) {
             set_error("ROW forward launch shape: at most 2 warps per block, within the device's shared memory");
             return SPH_EINVAL;
         }
-        return cuda_status(e, "ROW forward launch");
+        return cuda_status(e, ddsph ? "ROW Hessian forward launch" : "ROW forward launch");
     }
     if (!valid_lanes(a.launch)) return SPH_EINVAL;
     return cuda_status(slice_fwd(a), "SLICE forward launch");

@@ -62,7 +62,8 @@ const void* device_tables_down(int dtype);
 
 // Coefficient streams of the ROW kernels, FP32 (see sph_capi.cu): entry
 // (degree, slot, lane), lane fastest, kRowDegrees x kRowSlots x kRowLanes
-// float4 entries, then as many floats.
+// float4 entries {A, B, S, e}, then as many floats f, then as many float4
+// {g2, g3, g4, 0} (the second-derivative multipliers of the Hessian kernel).
 constexpr int kRowLanes = 8;
 constexpr int kRowDegrees = 64;
 constexpr int kRowSlots = 8;
@@ -198,6 +199,8 @@ int degree_fwd_down(const FwdArgs& a);
 // ROW kernels (FP32 arithmetic, 16 <= l_max <= 63, values and gradients):
 // part 0 covers 3..5 channels per lane (l_max <= 47), part 1 6..8.
 int row_fwd_part0(const FwdArgs& a);
+// FP32 forward with Hessians on the ROW decomposition (16 <= l_max <= 63).
+int row_hess_fwd(const FwdArgs& a);
 int row_fwd_part1(const FwdArgs& a);
 int row_bwd_part0(const BwdArgs& a);  // fused recompute-backward (dxyz), FP32
 int row_bwd_part1(const BwdArgs& a);

@@ -204,13 +204,14 @@ def test_argument_errors_before_any_cuda_call():
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 1, 0, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, hc, launch, 16, 32, 32, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 1, hc, launch, 16, none, none, none) == C.SPH_EUNSUPPORTED
-    # ROW: FP32 arithmetic, 16 <= l_max <= 63, no Hessians; backward (FP32) but no double backward
+    # ROW: FP32 arithmetic, 16 <= l_max <= 63; backward (FP32) but no double backward
     R = C.SPH_KERNEL_ROW
     assert _err(C.sphericart_compute_ex, 16, 4, 8, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 64, 0, 0, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 1, 0, 0, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 1, R, launch, 16, 32, none, none) == C.SPH_EUNSUPPORTED
-    assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 0, 0, R, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
+    # (ROW Hessians: FP32 storage only)
+    assert _err(C.sphericart_compute_ex, 16, 4, 20, 0, 0, 1, 0, R, launch, 16, 32, 48, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_backward, 16, 16, 4, 15, 0, 0, R, launch, 16, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_backward, 16, 16, 4, 20, 0, 1, R, launch, 16, none) == C.SPH_EUNSUPPORTED
     assert _err(C.sphericart_double_backward, 16, 16, 16, 4, 20, 0, 0, R, launch, 16, 16, none) == C.SPH_EUNSUPPORTED
