@@ -175,6 +175,20 @@ __global__ void __launch_bounds__(32 * kHMaxWarps) row_hess_kernel(const float* 
             s[i] = (kHSE - phase) % kHSE;
         }
 
+        // Coefficients of degree 0; with PF, later degrees are loaded one
+        // degree ahead (more registers, the loads off the critical path).
+        constexpr bool PF = NCH <= 5;
+        float4 ta[NCH], tg[NCH];
+        float tf[NCH];
+        if constexpr (PF) {
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                ta[k] = laneA[k * kRowLanes];
+                tf[k] = laneF[k * kRowLanes];
+                tg[k] = laneG[k * kRowLanes];
+            }
+        }
+
         int l = 0;
         bool first = true;
         while (l <= L) {
@@ -188,13 +202,25 @@ __global__ void __launch_bounds__(32 * kHMaxWarps) row_hess_kernel(const float* 
             while (true) {
                 const int ctr = d * d + d;
                 const int kend = d / kHG;  // channels m = j + 8k <= d need k <= d/8 (uniform)
+                float4 na[PF ? NCH : 1], ng[PF ? NCH : 1];
+                float nf[PF ? NCH : 1];
+                if constexpr (PF) {
+                    const int dn = d < L ? d + 1 : d;
+#pragma unroll
+                    for (int k = 0; k < NCH; ++k) {
+                        const int entn = (dn * kRowSlots + k) * kRowLanes;
+                        na[k] = laneA[entn];
+                        nf[k] = laneF[entn];
+                        ng[k] = laneG[entn];
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     if (k > kend) break;
                     const int ent = (d * kRowSlots + k) * kRowLanes;
-                    const float4 t0 = laneA[ent];  // {A, B, S, e}
-                    const float tf = laneF[ent];   // f
-                    const float4 tg = laneG[ent];  // {g2, g3, g4, 0}
+                    const float4 t0 = PF ? ta[k] : laneA[ent];  // {A, B, S, e}
+                    const float tfk = PF ? tf[k] : laneF[ent];  // f
+                    const float4 tgk = PF ? tg[k] : laneG[ent];  // {g2, g3, g4, 0}
                     // what this lane sends for the receivers of channel m+1 (lane j-1, or
                     // lane 7 from lane 0's next slot) and m+2 (lane j-2, or lanes 6, 7
                     // from lanes 0, 1's next slot)
@@ -210,10 +236,10 @@ __global__ void __launch_bounds__(32 * kHMaxWarps) row_hess_kernel(const float* 
                         QParts<float> qp;
                         qp.Q = q;
                         qp.E1 = t0.w * q1n;
-                        qp.Qz = tf * q1[k];
-                        qp.G2 = tg.x * q2nn;
-                        qp.G3 = tg.y * q2n;
-                        qp.G4 = tg.z * q2[k];
+                        qp.Qz = tfk * q1[k];
+                        qp.G2 = tgk.x * q2nn;
+                        qp.G3 = tgk.y * q2n;
+                        qp.G4 = tgk.z * q2[k];
                         Deriv<float> dc, ds;
                         assemble_m<true, true>(qp, x, y, float(m), float(m - 1), cm[k], sm[k], cm1[k], sm1[k],
                                                cm2[k], sm2[k], dc, ds);
@@ -226,6 +252,14 @@ __global__ void __launch_bounds__(32 * kHMaxWarps) row_hess_kernel(const float* 
                     }
                     q2[k] = q1[k];
                     q1[k] = q;
+                }
+                if constexpr (PF) {
+#pragma unroll
+                    for (int k = 0; k < NCH; ++k) {
+                        ta[k] = na[k];
+                        tf[k] = nf[k];
+                        tg[k] = ng[k];
+                    }
                 }
                 ++d;
                 if (d > L) break;
