@@ -321,7 +321,9 @@ int launch_row_hess(const FwdArgs& a) {
     if (!rt) return int(cudaErrorMemoryAllocation);
     auto kern = row_hess_kernel<NCH, NORM, CAP>;
     const size_t per_warp = row_hess_warp_bytes<CAP>();
-    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : kHMaxWarps;
+    // default (measured on GB300): 1-warp blocks with the coefficient
+    // prefetch (l_max <= 39), 2-warp blocks without it
+    const int W = a.launch.warps_per_block > 0 ? a.launch.warps_per_block : (NCH <= 5 ? 1 : kHMaxWarps);
     if (W > kHMaxWarps) return int(cudaErrorInvalidConfiguration);
     const size_t smem = size_t(W) * per_warp;
     if (smem > size_t(max_smem_optin())) return int(cudaErrorInvalidConfiguration);
@@ -354,8 +356,8 @@ int launch_row_hess(const FwdArgs& a) {
 // Window capacity (lanes_per_point): 0 or 2 = 136 columns, 1 = the least
 // that holds one degree of l_max (16 NCH + 8 columns: the most resident
 // warps), 3 = 256 columns (runs of ~1 KB, 4 warps per SM). Measured on GB300
-// (FP32, 40k-100k points, l_max 17..63): 136 columns with 2-warp blocks is
-// fastest or equal everywhere (2.0-2.7 TB/s; SLICE 1.5-1.9).
+// (FP32, 40k-100k points, l_max 17..63): 136 columns is fastest or equal
+// everywhere (2.0-2.9 TB/s; SLICE 1.5-1.9).
 template <int NCH, bool NORM>
 int launch_row_hess_cap(const FwdArgs& a) {
     const int pol = a.launch.lanes_per_point;
