@@ -79,9 +79,10 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
 /* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
  * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 12); else
- * POINT when l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for
- * FP32 arithmetic up to l_max 63 (with Hessians: FP32 storage); else DEGREE
- * for bfloat16 storage without Hessians; else SLICE.
+ * ROW for FP32 Hessians with FP32 storage from l_max 12 to 63; else POINT when
+ * l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for FP32
+ * arithmetic up to l_max 63; else DEGREE for bfloat16 storage without
+ * Hessians; else SLICE.
  *   POINT:  one thread per point, the whole (l, m) recursion unrolled in
  *           registers for a compile-time l_max, outputs staged in shared memory
  *           and written with bulk (TMA) copies.
@@ -96,8 +97,8 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
  *           recursion of Eq. iter-q-alt (its printed overall sign corrected:
  *           Q_l^m = -[2(m+1) z Q_l^{m+1} + (x^2+y^2) Q_l^{m+2}]/((l+m+1)(l-m)))
  *           from the tabulated Q_l^l; the paper's one-degree-at-a-time form.
- *   ROW:    FP32 arithmetic, 16 <= l_max <= 63, values, gradients and
- *           Hessians (FP32 storage): 8 lanes per point (lane j owns the
+ *   ROW:    FP32 arithmetic, 16 <= l_max <= 63, values and gradients, or
+ *           0 <= l_max <= 63 with Hessians (FP32 storage): 8 lanes per point (lane j owns the
  *           channels m = j mod 8, recursion state in registers, degree l
  *           uniform across the lanes); each point's output rows are staged in
  *           shared memory in windows of whole degrees and written with TMA

@@ -308,9 +308,10 @@ sph_launch default_point16_fwd(int L) {
 // Whether the POINT default runs FP32 Hessians on 16 lanes per point.
 // Measured on GB300 (1M / 400k / 200k points, l_max 4..16): faster for the
 // scaled form at l_max 8..10 (+6..10 %) and for the normalized form from
-// l_max 9 (1.4..2.3x at l_max 10..16); the one-lane tile is faster elsewhere.
+// l_max 9 (2.3x at l_max 10); the one-lane tile is faster below; from l_max
+// 12 AUTO runs ROW.
 bool point16_default(int L, int hess, int normalized, int dtype, int out) {
-    if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME) return false;
+    if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME || L >= kRowHessMinAuto) return false;
     return normalized ? L >= 9 : (L >= 8 && L <= 10);
 }
 
@@ -440,8 +441,10 @@ int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) 
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
     if (!hess && (mixed || (dtype == SPH_F64 && l_max >= 12))) return SPH_KERNEL_DEGREE;
     if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
+    // FP32 Hessians from l_max 12: ROW (2.1-2.9 TB/s; POINT 0.6-2.0 at l_max 12-16)
+    if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max >= kRowHessMinAuto && l_max <= kRowMaxL)
+        return SPH_KERNEL_ROW;
     if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
-    if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && dtype == SPH_F32 && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
     if (!hess && out == SPH_OUT_BF16) return SPH_KERNEL_DEGREE;
     return SPH_KERNEL_SLICE;
@@ -558,10 +561,10 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
         set_error("POINT kernels take l_max <= %d, native Q precision, and no bf16 Hessians", SPH_MAX_L_POINT);
         return SPH_EUNSUPPORTED;
     }
-    if (fam == SPH_KERNEL_ROW && (mixed || dtype != SPH_F32 || l_max < kRowMinL || l_max > kRowMaxL ||
-                                  (ddsph && out != SPH_OUT_SAME))) {
-        set_error("ROW kernels take FP32 arithmetic, %d <= l_max <= %d (Hessians with FP32 storage)", kRowMinL,
-                  kRowMaxL);
+    if (fam == SPH_KERNEL_ROW && (mixed || dtype != SPH_F32 || l_max < (ddsph ? 0 : kRowMinL) ||
+                                  l_max > kRowMaxL || (ddsph && out != SPH_OUT_SAME))) {
+        set_error("ROW kernels take FP32 arithmetic, %d <= l_max <= %d (with Hessians 0 <= l_max <= %d, FP32 "
+                  "storage)", kRowMinL, kRowMaxL, kRowMaxL);
         return SPH_EUNSUPPORTED;
     }
     const bool degree = fam == SPH_KERNEL_DEGREE || fam == SPH_KERNEL_DEGREE_DOWN;

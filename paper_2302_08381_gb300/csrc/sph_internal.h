@@ -199,8 +199,11 @@ int degree_fwd_down(const FwdArgs& a);
 // ROW kernels (FP32 arithmetic, 16 <= l_max <= 63, values and gradients):
 // part 0 covers 3..5 channels per lane (l_max <= 47), part 1 6..8.
 int row_fwd_part0(const FwdArgs& a);
-// FP32 forward with Hessians on the ROW decomposition (16 <= l_max <= 63).
+// FP32 forward with Hessians on the ROW decomposition (0 <= l_max <= 63).
 int row_hess_fwd(const FwdArgs& a);
+// Smallest l_max at which AUTO runs FP32 Hessians on ROW (measured on GB300:
+// 1.1-3.8x the POINT forms from l_max 12, slower at l_max <= 10).
+constexpr int kRowHessMinAuto = 12;
 int row_fwd_part1(const FwdArgs& a);
 int row_bwd_part0(const BwdArgs& a);  // fused recompute-backward (dxyz), FP32
 int row_bwd_part1(const BwdArgs& a);

@@ -1,4 +1,4 @@
-// ROW Hessians: FP32 values, gradients and Hessians for 16 <= l_max <= 63 on
+// ROW Hessians: FP32 values, gradients and Hessians for 0 <= l_max <= 63 on
 // the ROW decomposition (see sph_row.cu): 8 lanes per point, lane j owning
 // the m channels m = j (mod 8), the degree l outermost and uniform across the
 // warp, recursion state in registers, and each point's 13 output rows (value,
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(32 * kHMaxWarps) row_hess_kernel(const float* 
 #pragma unroll
                 for (int i = 0; i < kHPlanes; ++i) {
                     float* gr = hess_row(sph, dsph, ddsph, p, K, i);
-                    if (first)
-                        for (int c = j; c < s[i]; c += kHG) gr[c] = pst[i * BUF + c - s[i] + kHSE];
+                    if (first)  // the head, within the row (K < 8 at l_max <= 1)
+                        for (int c = j; c < min(s[i], c_hi); c += kHG) gr[c] = pst[i * BUF + c - s[i] + kHSE];
                     if (last)
                         for (int c = e[i] + j; c < c_hi; c += kHG) gr[c] = pst[i * BUF + c - s[i] + kHSE];
                 }
@@ -375,6 +375,10 @@ int launch_row_hess_norm(const FwdArgs& a) {
 
 int row_hess_fwd(const FwdArgs& a) {
     switch ((a.l_max + 1 + kHG - 1) / kHG) {
+        case 1:
+            return launch_row_hess_norm<1>(a);
+        case 2:
+            return launch_row_hess_norm<2>(a);
         case 3:
             return launch_row_hess_norm<3>(a);
         case 4:

@@ -95,15 +95,18 @@ def test_launch_shapes_and_limits():
 
 def test_auto_default():
     """AUTO runs 16 lanes per point for FP32 Hessians where measured faster
-    (scaled l_max 8..10, normalized from 9) and the one-lane tile elsewhere."""
+    (scaled l_max 8..10, normalized 9..11), the one-lane tile below, ROW from
+    l_max 12."""
     fam, s = C.sphericart_launch_info(8, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
     assert fam == C.SPH_KERNEL_POINT and s.lanes_per_point == 16
     fam, s = C.sphericart_launch_info(6, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
     assert s.lanes_per_point == 0
     fam, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 1)
     assert s.lanes_per_point == 0
+    fam, s = C.sphericart_launch_info(12, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
+    assert fam == C.SPH_KERNEL_ROW
     x = _t(inputs.shell_points(1000, 0.5, 2.0, seed=335))
-    for l_max, normalized in ((8, False), (12, True)):
+    for l_max, normalized in ((8, False), (10, True)):
         a = api.spherical_harmonics(x, l_max, normalized, gradients=True, hessians=True)
         b = api.spherical_harmonics(x, l_max, normalized, gradients=True, hessians=True, kernel="point",
                                     launch=_sixteen())

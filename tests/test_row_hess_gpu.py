@@ -1,4 +1,4 @@
-"""ROW Hessians (FP32 values, gradients and Hessians for 16 <= l_max <= 63 on
+"""ROW Hessians (FP32 values, gradients and Hessians for 0 <= l_max <= 63 on
 the 8-lanes-per-point ROW decomposition) against the FP64 oracle's analytic
 Hessians, through the C-ABI: scaled and normalized, pole neighbourhoods,
 both window capacities, ragged tails and output bounds."""
@@ -34,7 +34,7 @@ def test_against_oracle(normalized):
     1e-9..1e-4 rad from the poles."""
     x = np.concatenate([inputs.shell_points(90 + 3, 0.7, 2.0, seed=340).astype(np.float64),
                         inputs.pole_mix_points(30, seed=341) * 1.2]).astype(np.float32).astype(np.float64)
-    for l_max in (16, 17, 20, 23, 31, 32, 40, 47, 48, 55, 63):
+    for l_max in (0, 1, 2, 5, 7, 8, 12, 15, 16, 17, 20, 23, 31, 32, 40, 47, 48, 55, 63):
         v, g, H = _run(x, l_max, normalized)
         lv = np.arange(l_max + 1)
         rv, rg = oracle.spherical_harmonics_grad(x, l_max, normalized)
@@ -72,7 +72,11 @@ def test_matches_slice():
 
 @pytest.mark.parametrize("n", [0, 1, 5, 9])
 def test_edge_sizes_and_bounds(n):
-    for l_max in (16, 33):
+    # l_max 0 and 1: rows shorter than one 32-byte sector (the unaligned head
+    # must stay inside the row)
+    for l_max in (0, 1, 2, 16, 33):
+        if n == 0 and l_max < 16:
+            continue  # empty outputs pass NULL: a gradients-only request, which ROW serves from l_max 16
         K = (l_max + 1) ** 2
         x = inputs.normal_points(max(n, 1), seed=344)[:n].astype(np.float32)
         big = [torch.full((n + 2, K), 7.0, device=DEV), torch.full((n + 2, 3, K), 7.0, device=DEV),
@@ -95,6 +99,8 @@ def test_limits():
         api.spherical_harmonics(x, 20, gradients=True, hessians=True, kernel="row", out_dtype=torch.bfloat16)
     with pytest.raises(C.SphericartError):  # FP64
         api.spherical_harmonics(x.double(), 20, gradients=True, hessians=True, kernel="row")
+    with pytest.raises(C.SphericartError):  # gradients without Hessians below l_max 16
+        api.spherical_harmonics(x, 12, gradients=True, kernel="row")
     with pytest.raises(C.SphericartError):  # beyond l_max 63
         api.spherical_harmonics(x, 64, gradients=True, hessians=True, kernel="row")
     with pytest.raises(C.SphericartError):  # 3 warps per block
