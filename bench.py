@@ -807,6 +807,9 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (200_000, 50, "l50_grad_f64_norm_n200k_degree_down",
          dict(gradients=True, normalized=True, kernel="degree_down"), 8, 4),
         (1_000_000, 16, "l16_grad_f64_n1M", dict(gradients=True), 8, 4),
+        # FP64 with gradients from l_max 9: AUTO runs DEGREE (2 lanes per point)
+        (1_000_000, 10, "l10_grad_f64_n1M", dict(gradients=True), 8, 4),
+        (1_000_000, 10, "l10_grad_f64_n1M_point", dict(gradients=True, kernel="point"), 8, 4),
         # hard-coded l <= 3 + recursion (POINT_HC, AUTO's FP64 choice up to l_max 8
         # with gradients, 3 for values) against the all-recursion POINT kernel
         (1_000_000, 3, "l3_grad_f64_n1M_point", dict(gradients=True, kernel="point"), 8, 4),

@@ -410,10 +410,11 @@ bool valid_lanes(const sph_launch& s) {
 bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
 // Lanes per point of the upward DEGREE kernel when the caller leaves it 0
-// (measured on GB300: FP64 prefers 2 lanes per point up to l_max ~ 24 and 4
-// above, FP32 arithmetic with FP64 Q ("mixed") 2, FP32 / bf16 storage 4).
+// (measured on GB300: FP64 prefers 1 lane per point below l_max 10, 2 up to
+// l_max ~ 24 and 4 above, FP32 arithmetic with FP64 Q ("mixed") 2, FP32 /
+// bf16 storage 4).
 int degree_default_lpp(int l_max, int dtype, int qprec) {
-    if (dtype == SPH_F64) return l_max >= 24 ? 4 : (l_max >= 12 ? 2 : 1);
+    if (dtype == SPH_F64) return l_max >= 24 ? 4 : (l_max >= 10 ? 2 : 1);
     if (qprec == SPH_Q_F64) return 2;
     return 4;
 }
@@ -439,7 +440,9 @@ namespace {
 // (DEGREE for bf16 storage).
 int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
-    if (!hess && (mixed || (dtype == SPH_F64 && l_max >= 12))) return SPH_KERNEL_DEGREE;
+    // FP64: DEGREE from l_max 12, and with gradients from l_max 9 (measured:
+    // l_max 10 / 11 with gradients 1.65x / 2.0x POINT; values stay on POINT)
+    if (!hess && (mixed || (dtype == SPH_F64 && (l_max >= 12 || (grad && l_max >= 9))))) return SPH_KERNEL_DEGREE;
     if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
     // FP32 Hessians from l_max 12: ROW (2.1-2.9 TB/s; POINT 0.6-2.0 at l_max 12-16)
     if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max >= kRowHessMinAuto && l_max <= kRowMaxL)

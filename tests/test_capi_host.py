@@ -143,11 +143,17 @@ def test_host_downward_tables_reproduce_oracle():
 
 
 def test_auto_family_choice():
-    """AUTO: DEGREE for FP64 arithmetic from l_max 12; ROW for FP32
-    arithmetic from POINT's range to l_max 63; then SLICE (FP32 storage) or
-    DEGREE (bf16 storage); Hessians on SLICE (host-only query)."""
+    """AUTO: DEGREE for FP64 arithmetic from l_max 12 (with gradients from
+    9); ROW for FP32 arithmetic from POINT's range to l_max 63 and for FP32
+    Hessians from l_max 12; then SLICE (FP32 storage) or DEGREE (bf16
+    storage); FP64 Hessians on SLICE (host-only query)."""
     fam, shape = C.sphericart_launch_info(16, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
     assert fam == C.SPH_KERNEL_DEGREE and shape.lanes_per_point in (1, 2, 4)
+    fam, shape = C.sphericart_launch_info(10, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
+    assert fam == C.SPH_KERNEL_DEGREE and shape.lanes_per_point == 2
+    assert C.sphericart_launch_info(9, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_DEGREE
+    assert C.sphericart_launch_info(10, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT  # values
+    assert C.sphericart_launch_info(20, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)[0] == C.SPH_KERNEL_ROW  # FP32 Hessians
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_BF16, 1, 0)
     assert fam == C.SPH_KERNEL_ROW
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)
@@ -292,10 +298,10 @@ def test_point_default_shapes():
     assert fam == C.SPH_KERNEL_POINT_HC and (s.points_per_tile, s.warps_per_block, s.blocks_per_sm) == (28, 1, 16)
     assert C.sphericart_launch_info(3, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT_HC
     assert C.sphericart_launch_info(4, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT
-    assert C.sphericart_launch_info(9, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_POINT
+    assert C.sphericart_launch_info(9, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_DEGREE  # gradients from 9
     assert C.sphericart_launch_info(3, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)[0] == C.SPH_KERNEL_POINT
     assert 28 * 4 * 81 * 8 <= 74 * 1024 < 30 * 4 * 81 * 8  # the largest even tile inside 74 KB
     _, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)
     assert (s.points_per_tile, s.warps_per_block) == (32, 1)
-    _, s = C.sphericart_launch_info(11, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
-    assert (s.points_per_tile, s.warps_per_block) == (16, 1)
+    fam, s = C.sphericart_launch_info(11, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)  # DEGREE from l_max 9 with gradients
+    assert fam == C.SPH_KERNEL_DEGREE and s.lanes_per_point == 2
