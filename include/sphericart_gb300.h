@@ -78,7 +78,7 @@ typedef enum { SPH_OUT_SAME = 0, SPH_OUT_BF16 = 1 } sph_out;
 typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 
 /* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
- * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 12, with
+ * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 14, with
  * gradients from l_max 9); else
  * ROW for FP32 Hessians with FP32 storage from l_max 12 to 63; else POINT when
  * l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for FP32

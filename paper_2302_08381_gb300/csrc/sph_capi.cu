@@ -440,9 +440,10 @@ namespace {
 // (DEGREE for bf16 storage).
 int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
-    // FP64: DEGREE from l_max 12, and with gradients from l_max 9 (measured:
-    // l_max 10 / 11 with gradients 1.65x / 2.0x POINT; values stay on POINT)
-    if (!hess && (mixed || (dtype == SPH_F64 && (l_max >= 12 || (grad && l_max >= 9))))) return SPH_KERNEL_DEGREE;
+    // FP64: DEGREE with gradients from l_max 9 (measured at 1M-4M points:
+    // l_max 10 / 11 at 1.65x / 2.0x POINT), values from l_max 14 (POINT 8 %
+    // faster at l_max 12, equal at 13; at 10k points POINT up to 16)
+    if (!hess && (mixed || (dtype == SPH_F64 && (l_max >= 14 || (grad && l_max >= 9))))) return SPH_KERNEL_DEGREE;
     if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
     // FP32 Hessians from l_max 12: ROW (2.1-2.9 TB/s; POINT 0.6-2.0 at l_max 12-16)
     if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max >= kRowHessMinAuto && l_max <= kRowMaxL)
