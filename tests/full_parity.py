@@ -43,6 +43,19 @@ def _fwd_chunk(job):
     return ev, eg, finite
 
 
+def _hess_chunk(job):
+    import oracle
+    from parity_utils import hess_errors
+
+    a, b, l_max, normalized = job
+    x = np.asarray(_ARR["xyz"][a:b], dtype=np.float64)
+    ref = oracle.spherical_harmonics_hessian(x, l_max, normalized)
+    got = np.asarray(_ARR["ddsph"][a:b], np.float64)
+    eh = hess_errors(got, ref, x, l_max, normalized)
+    sym = bool(np.array_equal(got, got.transpose(0, 2, 1, 3)))
+    return eh, bool(np.all(np.isfinite(got))), sym
+
+
 def _bwd_chunk(job):
     import oracle
 
@@ -121,3 +134,16 @@ def adjoint_errors(xyz, g, l_max, normalized, dxyz=None, v=None, grad_g=None, gr
         ref = max(r[i][1] for r in res)
         out[name] = diff / max(ref, 1e-300)
     return out
+
+
+def hessian_errors(xyz, l_max, normalized, ddsph, processes=None):
+    """Per-l maximum Hessian error over every point (``parity_utils`` scale),
+    whether every output is finite, and whether every point's [3, 3] planes
+    are symmetric bit for bit. ``ddsph`` [n, 3, 3, K] numpy (any float
+    dtype; staged as given)."""
+    n = xyz.shape[0]
+    K = (l_max + 1) ** 2
+    jobs = [(a, b, l_max, bool(normalized)) for a, b in _chunks(n, 9 * K)]
+    res = _pool_map({"xyz": xyz, "ddsph": ddsph}, _hess_chunk, jobs, processes)
+    eh = np.max(np.stack([r[0] for r in res]), axis=0)
+    return eh, all(r[1] for r in res), all(r[2] for r in res)

@@ -35,3 +35,20 @@ def test_adjoint_errors_match_direct_evaluation():
     err = full_parity.adjoint_errors(x, g, l_max, False, dxyz=dx, v=v, grad_g=gg, grad_xyz=gx_bad, processes=2)
     assert err["dxyz"] < 1e-15 and err["grad_g"] < 1e-15
     assert abs(err["grad_xyz"] - 1e-3) < 1e-9
+
+
+def test_hessian_pool_finds_a_planted_error():
+    """The Hessian pool reproduces the oracle on exact inputs (error 0), and
+    one wrong element or one broken symmetric pair is found."""
+    import oracle
+
+    x = inputs.shell_points(700, 0.5, 2.0, seed=52).astype(np.float64)
+    L = 5
+    H = oracle.spherical_harmonics_hessian(x, L, True)
+    H = 0.5 * (H + H.transpose(0, 2, 1, 3))  # the oracle's entries (i, k), (k, i) differ in rounding
+    eh, finite, sym = full_parity.hessian_errors(x, L, True, H, processes=2)
+    assert finite and sym and np.all(eh < 1e-14)
+    H2 = H.copy()
+    H2[613, 1, 2, 20] += 1e-3 * abs(H2[613, 1, 2, 20]) + 1e-6  # l = 4 block
+    eh2, _, sym2 = full_parity.hessian_errors(x, L, True, H2, processes=2)
+    assert eh2[4] > 1e-9 and np.all(np.delete(eh2, 4) < 1e-14) and not sym2

@@ -111,3 +111,17 @@ def test_auto_default():
         b = api.spherical_harmonics(x, l_max, normalized, gradients=True, hessians=True, kernel="point",
                                     launch=_sixteen())
         assert all(torch.equal(u, w) for u, w in zip(a, b)), (l_max, normalized)
+
+
+def test_full_size_lmax8_every_point():
+    """400,000 points, l_max 8, scaled, FP32 Hessians on the AUTO path (16
+    lanes per point): every element of ddsph against the oracle, symmetric
+    planes bit for bit."""
+    import full_parity
+
+    n, l_max = 400_000, 8
+    x = inputs.shell_points(n, 0.5, 5.0, seed=336).astype(np.float32)
+    _, _, H = api.spherical_harmonics(_t(x), l_max, False, gradients=True, hessians=True)
+    eh, finite, sym = full_parity.hessian_errors(x.astype(np.float64), l_max, False, H.cpu().numpy())
+    assert finite and sym
+    assert np.all(eh <= 5e-6 * (np.arange(l_max + 1) + 1)), eh

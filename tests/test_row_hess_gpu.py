@@ -105,3 +105,17 @@ def test_limits():
         api.spherical_harmonics(x, 64, gradients=True, hessians=True, kernel="row")
     with pytest.raises(C.SphericartError):  # 3 warps per block
         api.spherical_harmonics(x, 20, gradients=True, hessians=True, kernel="row", launch=C.make_launch(0, 3, 0, 0))
+
+
+def test_full_size_lmax20_every_point():
+    """100,000 points (half within 1e-4 rad of the poles), l_max 20,
+    normalized, FP32 Hessians on the AUTO path (ROW): every element of ddsph
+    against the oracle, symmetric planes bit for bit."""
+    import full_parity
+
+    n, l_max = 100_000, 20
+    x = inputs.pole_mix_points(n, seed=346).astype(np.float32)
+    _, _, H = api.spherical_harmonics(_t(x), l_max, True, gradients=True, hessians=True)
+    eh, finite, sym = full_parity.hessian_errors(x.astype(np.float64), l_max, True, H.cpu().numpy())
+    assert finite and sym
+    assert np.all(eh <= 5e-6 * (np.arange(l_max + 1) + 1)), eh
