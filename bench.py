@@ -763,14 +763,32 @@ def run_variants_leg(torch, api, inputs, dev, stream, flush):
         (4_194_304, 8, "l8_grad_f64", dict(gradients=True), 8, 4),
         (1_048_576, 8, "l8_grad_hess_f32", dict(gradients=True, hessians=True), 4, 13),
         (1_048_576, 8, "l8_grad_hess_f32_slice", dict(gradients=True, hessians=True, kernel="slice"), 4, 13),
-        # FP32 Hessians: AUTO runs 16 lanes per point (one per output plane) at
-        # scaled l_max 8..10 and normalized from 9; the one-lane tile beside it
+        # FP32 Hessians: AUTO runs 10 lanes per point (one per distinct plane)
+        # at scaled l_max 7..16 and normalized 6..13, ROW above; the one-lane
+        # tile, the 16-lane map and ROW beside it
         (1_048_576, 8, "l8_grad_hess_f32_one_lane",
          dict(gradients=True, hessians=True, kernel="point", launch=(12, 2, 16, 1)), 4, 13),
+        (1_048_576, 8, "l8_grad_hess_f32_sixteen_lanes",
+         dict(gradients=True, hessians=True, kernel="point", launch=(4, 0, 0, 16)), 4, 13),
+        (400_000, 10, "l10_grad_hess_f32_norm_n400k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
+        (400_000, 10, "l10_grad_hess_f32_norm_n400k_sixteen_lanes",
+         dict(gradients=True, hessians=True, normalized=True, kernel="point", launch=(4, 0, 0, 16)), 4, 13),
         (400_000, 12, "l12_grad_hess_f32_norm_n400k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
         (100_000, 20, "l20_grad_hess_f32_norm_n100k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
         (400_000, 12, "l12_grad_hess_f32_norm_n400k_one_lane",
          dict(gradients=True, hessians=True, normalized=True, kernel="point", launch=(4, 1, 0, 1)), 4, 13),
+        (400_000, 12, "l12_grad_hess_f32_norm_n400k_row",
+         dict(gradients=True, hessians=True, normalized=True, kernel="row"), 4, 13),
+        (200_000, 15, "l15_grad_hess_f32_n200k", dict(gradients=True, hessians=True), 4, 13),
+        (200_000, 15, "l15_grad_hess_f32_n200k_row", dict(gradients=True, hessians=True, kernel="row"), 4, 13),
+        (200_000, 16, "l16_grad_hess_f32_n200k", dict(gradients=True, hessians=True), 4, 13),
+        (200_000, 16, "l16_grad_hess_f32_n200k_row", dict(gradients=True, hessians=True, kernel="row"), 4, 13),
+        (200_000, 13, "l13_grad_hess_f32_norm_n200k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
+        (200_000, 13, "l13_grad_hess_f32_norm_n200k_row",
+         dict(gradients=True, hessians=True, normalized=True, kernel="row"), 4, 13),
+        (200_000, 14, "l14_grad_hess_f32_norm_n200k", dict(gradients=True, hessians=True, normalized=True), 4, 13),
+        (200_000, 14, "l14_grad_hess_f32_norm_n200k_ten_lanes",
+         dict(gradients=True, hessians=True, normalized=True, kernel="point", launch=(3, 0, 0, 10)), 4, 13),
         (1_000_000, 10, "l10_grad_f32_n1M", dict(gradients=True), 4, 4),
         (1_000_000, 10, "l10_grad_bf16_n1M", dict(gradients=True, out_dtype=torch.bfloat16), 2, 4),
         # l_max 12..16 (AUTO: 4 lanes per point, one per output plane) against

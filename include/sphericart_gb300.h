@@ -80,7 +80,9 @@ typedef enum { SPH_Q_NATIVE = 0, SPH_Q_F64 = 1 } sph_qprec;
 /* Kernel family. AUTO picks, by measurement on GB300: DEGREE for FP64
  * arithmetic without Hessians (the mixed mode; SPH_F64 from l_max 14, with
  * gradients from l_max 9); else
- * ROW for FP32 Hessians with FP32 storage from l_max 12 to 63; else POINT when
+ * ROW for FP32 Hessians with FP32 storage up to l_max 63, from l_max 14 in
+ * the normalized form and beyond SPH_MAX_L_POINT in the scaled one
+ * (launch_info reports the scaled form's choice); else POINT when
  * l_max <= SPH_MAX_L_POINT (except bfloat16 Hessians); else ROW for FP32
  * arithmetic up to l_max 63; else DEGREE for bfloat16 storage without
  * Hessians; else SLICE.
@@ -132,9 +134,13 @@ typedef enum {
  *                    (value, d/dx, d/dy, d/dz) of each point, points_per_tile
  *                    <= 8: every lane busy where one-lane tiles that fit
  *                    shared memory are short (FP32 arithmetic, gradients, no
- *                    Hessians), or 16 = one lane per plane of the value,
- *                    gradient and 3x3 Hessian (FP32 Hessians, FP32 storage;
- *                    points_per_tile even and <= 8, warps_per_block <= 4);
+ *                    Hessians), 10 = one lane per distinct plane of the
+ *                    value, gradient and symmetric Hessian, three points
+ *                    per warp pass, off-diagonal lanes writing both mirrors
+ *                    (FP32 Hessians, FP32 storage; points_per_tile 3, 6, 9
+ *                    or 12, warps_per_block <= 4; any output alignment), or
+ *                    16 = one lane per plane of the value, gradient and 3x3
+ *                    Hessian (same limits; points_per_tile even and <= 8);
  *                    SLICE: 8, 16 or 32 (0 = by l_max)
  * DEGREE kernels read warps_per_block (0..8, 0 = by shared memory),
  * blocks_per_sm and lanes_per_point (1, 2 or 4 lanes per point for DEGREE, 0 =
@@ -146,8 +152,8 @@ typedef enum {
  * The POINT default (no shape given and none tuned) fills ~48 KB tiles (FP32,
  * bf16) or up to 32 points in <= 74 KB with one warp per block (FP64, bound by
  * the FP64 pipe), and with FP32 gradients from l_max 10 runs 4 lanes per
- * point on 8-point tiles, with FP32 Hessians 16 lanes per point where that
- * measured faster (scaled l_max 8..10, normalized from l_max 9); when a call
+ * point on 8-point tiles, with FP32 Hessians 10 lanes per point where that
+ * measured faster (scaled l_max 7..16, normalized 6..13; ROW above); when a call
  * has fewer than 2 x SMs x
  * warps_per_block tiles, it runs fewer warps per block so that the blocks
  * reach every SM.                                                           */

@@ -305,14 +305,48 @@ sph_launch default_point16_fwd(int L) {
     return sph_launch{4, W, 0, 16};
 }
 
-// Whether the POINT default runs FP32 Hessians on 16 lanes per point.
-// Measured on GB300 (1M / 400k / 200k points, l_max 4..16): faster for the
-// scaled form at l_max 8..10 (+6..10 %) and for the normalized form from
-// l_max 9 (2.3x at l_max 10); the one-lane tile is faster below; from l_max
-// 12 AUTO runs ROW.
-bool point16_default(int L, int hess, int normalized, int dtype, int out) {
-    if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME || L >= kRowHessMinAuto) return false;
-    return normalized ? L >= 9 : (L >= 8 && L <= 10);
+// Shared-memory bytes per warp of the 10-lanes-per-point Hessian tile of P
+// points (FP32): for odd K the three images with 4 floats of phase slack each,
+// for even K 10 row slots of stride point4_stride per point.
+size_t point10_tile_bytes(int L, int P) {
+    const size_t K = size_t(L + 1) * (L + 1);
+    if (K % 2 == 0) return 10 * size_t(P) * 4 * size_t(point4_stride(L, 4));
+    auto part = [](size_t e) { return (e + 4 + 3) / 4 * 4 * 4; };
+    return part(size_t(P) * K) + part(3 * size_t(P) * K) + part(9 * size_t(P) * K);
+}
+
+// Default shape of the 10-lanes-per-point Hessian tile (measured on GB300,
+// 1M / 400k / 200k points): to l_max 8, 6 points per tile (two passes) in
+// 2-warp blocks; above, 3 (one pass keeps more warps resident once the tile
+// outgrows the register-bound 12 warps per SM), in one-warp blocks for even K
+// (per-row copies) and for odd K (whole-image copies) in the largest block of
+// 4 or 2 warps that keeps as many warps resident as one-warp blocks would
+// (1.1x at l_max 10 and 12), else one warp.
+sph_launch default_point10_fwd(int L) {
+    if (L <= 8) return sph_launch{6, 2, 0, 10};
+    int W = 1;
+    if (((L + 1) * (L + 1)) % 2) {
+        const size_t tile = point10_tile_bytes(L, 3), smem = size_t(max_smem_optin());
+        const size_t best = std::min<size_t>(12, smem / tile);
+        for (int w : {4, 2}) {
+            if (w * (smem / (w * tile)) >= best) {
+                W = w;
+                break;
+            }
+        }
+    }
+    return sph_launch{3, W, 0, 10};
+}
+
+// Whether the POINT default runs FP32 Hessians on 10 lanes per point.
+// Measured on GB300 (1M points to l_max 8, 400k / 200k above): faster than
+// the one-lane tile and the 16-lane map for the scaled form from l_max 7
+// (1.1x the 16-lane map at l_max 8, 2.3x at 11, 3.6x at 16) and for the
+// normalized form from l_max 6 (1.2-1.6x); the one-lane tile is faster below;
+// AUTO runs ROW from row_hess_min_auto.
+bool point10_default(int L, int hess, int normalized, int dtype, int out) {
+    if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME || L >= row_hess_min_auto(normalized)) return false;
+    return L >= (normalized ? 6 : 7);
 }
 
 // Whether the POINT default (no shape given, none tuned) runs 4 lanes per
@@ -438,15 +472,16 @@ namespace {
 // lanes) is fastest; beyond POINT's range FP32 arithmetic runs on ROW up to
 // its l_max 63 (1.8-2.2x SLICE; FP32 Hessians 1.2-1.7x), then on SLICE
 // (DEGREE for bf16 storage).
-int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad) {
+int auto_family(int l_max, int dtype, int out, int qprec, bool hess, bool grad, int normalized) {
     const bool mixed = dtype == SPH_F32 && qprec == SPH_Q_F64;
     // FP64: DEGREE with gradients from l_max 9 (measured at 1M-4M points:
     // l_max 10 / 11 at 1.65x / 2.0x POINT), values from l_max 14 (POINT 8 %
     // faster at l_max 12, equal at 13; at 10k points POINT up to 16)
     if (!hess && (mixed || (dtype == SPH_F64 && (l_max >= 14 || (grad && l_max >= 9))))) return SPH_KERNEL_DEGREE;
     if (!hess && point_hybrid_wins(l_max, dtype, grad)) return SPH_KERNEL_POINT_HC;
-    // FP32 Hessians from l_max 12: ROW (2.1-2.9 TB/s; POINT 0.6-2.0 at l_max 12-16)
-    if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max >= kRowHessMinAuto && l_max <= kRowMaxL)
+    // FP32 Hessians: ROW from l_max 13 (normalized) or beyond POINT's range
+    if (hess && dtype == SPH_F32 && out == SPH_OUT_SAME && l_max >= row_hess_min_auto(normalized) &&
+        l_max <= kRowMaxL)
         return SPH_KERNEL_ROW;
     if (l_max <= SPH_MAX_L_POINT && !(hess && out == SPH_OUT_BF16)) return SPH_KERNEL_POINT;
     if (!hess && dtype == SPH_F32 && l_max <= kRowMaxL) return SPH_KERNEL_ROW;
@@ -550,7 +585,8 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
     const int grad = dsph ? 1 : 0;
     int fam = kernel;
     const bool hess_bf16 = ddsph && out == SPH_OUT_BF16;
-    if (fam == SPH_KERNEL_AUTO) fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr, dsph != nullptr);
+    if (fam == SPH_KERNEL_AUTO)
+        fam = auto_family(l_max, dtype, out, qprec, ddsph != nullptr, dsph != nullptr, normalized);
     int hc = 0;
     if (fam == SPH_KERNEL_POINT_HC) {
         if (l_max > kHcMaxL || ddsph || mixed || out != SPH_OUT_SAME) {
@@ -611,13 +647,39 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             a.launch.blocks_per_sm == 0 && a.launch.lanes_per_point == 0) {
             if (point4_default(l_max, grad, eo, hess, hc))
                 a.launch.lanes_per_point = 4;
-            else if (point16_default(l_max, hess, normalized, dtype, out))
-                a.launch.lanes_per_point = 16;
+            else if (point10_default(l_max, hess, normalized, dtype, out))
+                a.launch.lanes_per_point = 10;
         }
         const int lpp = a.launch.lanes_per_point;
-        if (lpp != 0 && lpp != 1 && lpp != 4 && lpp != 16) {
-            set_error("POINT launch: lanes_per_point must be 0, 1, 4 or 16");
+        if (lpp != 0 && lpp != 1 && lpp != 4 && lpp != 10 && lpp != 16) {
+            set_error("POINT launch: lanes_per_point must be 0, 1, 4, 10 or 16");
             return SPH_EINVAL;
+        }
+        if (lpp == 10) {  // tiles of whole passes of three points, any start (no 16-byte tile multiple)
+            if (!hess || dtype != SPH_F32 || out != SPH_OUT_SAME || hc) {
+                set_error("POINT with 10 lanes per point takes FP32 arithmetic and storage with Hessians");
+                return SPH_EUNSUPPORTED;
+            }
+            const sph_launch d10 = default_point10_fwd(l_max);
+            sph_launch& s = a.launch;
+            if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = d10.blocks_per_sm;
+            if (s.points_per_tile == 0) s.points_per_tile = d10.points_per_tile;
+            if (s.warps_per_block == 0) s.warps_per_block = d10.warps_per_block;
+            if (s.points_per_tile < 3 || s.points_per_tile > 12 || s.points_per_tile % 3 || s.warps_per_block < 1 ||
+                s.warps_per_block > 4 || s.blocks_per_sm < 0 || s.blocks_per_sm > 32) {
+                set_error("POINT with 10 lanes per point: points_per_tile 3, 6, 9 or 12, warps_per_block <= 4");
+                return SPH_EINVAL;
+            }
+            if (size_t(s.warps_per_block) * point10_tile_bytes(l_max, s.points_per_tile) > size_t(max_smem_optin())) {
+                set_error("POINT with 10 lanes per point: the tile does not fit shared memory");
+                return SPH_EINVAL;
+            }
+            if (from_default) {
+                const int64_t tiles = (n + s.points_per_tile - 1) / s.points_per_tile;
+                const int64_t per_w = std::max<int64_t>(1, tiles / (2 * int64_t(sm_count())));
+                s.warps_per_block = int(std::min<int64_t>(s.warps_per_block, per_w));
+            }
+            return cuda_status(point_fwd_fn(l_max)(a), "POINT forward launch");
         }
         if (lpp == 4 && (!grad || hess || dtype != SPH_F32 || hc)) {
             set_error("POINT with 4 lanes per point takes FP32 arithmetic, values and gradients (no Hessians)");
@@ -834,7 +896,7 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
         return SPH_EINVAL;
     }
     const int eo = elem_size(dtype, out);
-    int fam = auto_family(l_max, dtype, out, SPH_Q_NATIVE, hess != 0, grad != 0);
+    int fam = auto_family(l_max, dtype, out, SPH_Q_NATIVE, hess != 0, grad != 0, 0);  // (the scaled form's choice)
     const bool hc = fam == SPH_KERNEL_POINT_HC;
     if (hc) fam = SPH_KERNEL_POINT;  // same launch shapes
     if (fam == SPH_KERNEL_DEGREE) {
@@ -860,12 +922,14 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess, in
                           s.lanes_per_point == 0;
         const bool four = s.lanes_per_point == 4 || (none && point4_default(l_max, grad, eo, hess, hc ? 1 : 0));
         // (the scaled form's choice: launch_info takes no normalized flag)
-        const bool sixteen = s.lanes_per_point == 16 || (none && !four && point16_default(l_max, hess, 0, dtype, out));
+        const bool ten = s.lanes_per_point == 10 || (none && !four && point10_default(l_max, hess, 0, dtype, out));
+        const bool sixteen = s.lanes_per_point == 16;
         const sph_launch dflt = four      ? default_point4_fwd(l_max, eo)
+                                : ten     ? default_point10_fwd(l_max)
                                 : sixteen ? default_point16_fwd(l_max)
                                           : default_point_fwd(l_max, grad ? 1 : 0, eo, hess ? 1 : 0);
         if (four) s.lanes_per_point = 4;
-        if (sixteen) s.lanes_per_point = 16;
+        if (ten) s.lanes_per_point = 10;
         // as resolve_point: no tuned shape at all takes the whole default
         if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = dflt.blocks_per_sm;
         if (s.points_per_tile == 0) s.points_per_tile = dflt.points_per_tile;

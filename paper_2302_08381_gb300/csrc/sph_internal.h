@@ -201,9 +201,16 @@ int degree_fwd_down(const FwdArgs& a);
 int row_fwd_part0(const FwdArgs& a);
 // FP32 forward with Hessians on the ROW decomposition (0 <= l_max <= 63).
 int row_hess_fwd(const FwdArgs& a);
-// Smallest l_max at which AUTO runs FP32 Hessians on ROW (measured on GB300:
-// 1.1-3.8x the POINT forms from l_max 12, slower at l_max <= 10).
-constexpr int kRowHessMinAuto = 12;
+// Smallest l_max at which AUTO runs FP32 Hessians on ROW (measured on GB300,
+// 400k / 200k points, against POINT with 10 lanes per point): normalized
+// from l_max 14 (ROW 1.2x at 14, equal at 15, 2.1x at 16; POINT 1.3-1.5x at
+// 12 and 13); the scaled form stays on POINT to its l_max 16 (1.1-2.2x ROW
+// at 12..16).
+constexpr int kRowHessMinAutoNormalized = 14;
+constexpr int kRowHessMinAutoScaled = SPH_MAX_L_POINT + 1;
+SPH_HD constexpr int row_hess_min_auto(int normalized) {
+    return normalized ? kRowHessMinAutoNormalized : kRowHessMinAutoScaled;
+}
 int row_fwd_part1(const FwdArgs& a);
 int row_bwd_part0(const BwdArgs& a);  // fused recompute-backward (dxyz), FP32
 int row_bwd_part1(const BwdArgs& a);

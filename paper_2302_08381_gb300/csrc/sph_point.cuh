@@ -569,11 +569,10 @@ __global__ void __launch_bounds__(256) point4_fwd_kernel(const T* __restrict__ x
 // role weights from the point's coordinates. The normalized form needs the
 // value and two gradient components of the same column: taken from the
 // point's lanes 0 and 1 + i by warp shuffles.
-template <int L, bool NORM, typename Tabs>
-__device__ __forceinline__ void point16_core(float x, float y, float z, float r2, const Tabs& tb, int lane,
-                                             float ir, float* __restrict__ rowp) {
-    const int r = lane & 15;
-    const int rr = r < 13 ? r : 12;
+template <int L, bool NORM, bool TWO = false, typename Tabs>
+__device__ __forceinline__ void point16_core(float x, float y, float z, float r2, const Tabs& tb, int rr, int base,
+                                             float ir, float* __restrict__ rowp, float* __restrict__ rowp2,
+                                             bool store) {
     const int hi = rr >= 4 ? (rr - 4) / 3 : 0, hk = rr >= 4 ? (rr - 4) % 3 : 0;
     // the symmetric entry (i, k) with i <= k selects the formula
     const int i0 = hi < hk ? hi : hk, k0 = hi < hk ? hk : hi;
@@ -621,8 +620,8 @@ __device__ __forceinline__ void point16_core(float x, float y, float z, float r2
     // Normalized form: plane' = sc (plane + wv v + wi g_i + wk g_k), v and g from
     // the point's lanes 0 and 1 + i / 1 + k (raw values at the unit point).
     // (i0, k0) for both (i, k) and (k, i): the two planes of a symmetric pair
-    // run the same operations and come out bit-identical
-    const int base = lane & 16;
+    // run the same operations and come out bit-identical; `base` is the lane
+    // of the point's value plane, base + 1 + i that of gradient component i
     const int src_i = base + 1 + i0, src_k = base + 1 + k0;
     const float ui = i0 == 0 ? x : (i0 == 1 ? y : z), uk = k0 == 0 ? x : (k0 == 1 ? y : z);
     const float ug = isgx ? x : (isgy ? y : z);  // gradient planes: u of their component
@@ -672,7 +671,10 @@ __device__ __forceinline__ void point16_core(float x, float y, float z, float r2
                     const float gk = __shfl_sync(0xffffffffu, out, src_k);
                     out = sc * (out + wv * v + wi * gi + wk * gk);
                 }
-                if (r < 13) rowp[l * l + l] = out;
+                if (store) {
+                    rowp[l * l + l] = out;
+                    if (TWO) rowp2[l * l + l] = out;
+                }
             } else {
                 const float Am = aQ * q[m] + A;
                 const float mB = float(m) * (bQ * q[m] + bE * E1 + bz * Qz);
@@ -695,9 +697,13 @@ __device__ __forceinline__ void point16_core(float x, float y, float z, float r2
                     oc = sc * (oc + wv * vc + wi * gic + wk * gkc);
                     os = sc * (os + wv * vs + wi * gis + wk * gks);
                 }
-                if (r < 13) {
+                if (store) {
                     rowp[l * l + l + m] = oc;
                     rowp[l * l + l - m] = os;
+                    if (TWO) {
+                        rowp2[l * l + l + m] = oc;
+                        rowp2[l * l + l - m] = os;
+                    }
                 }
             }
         }
@@ -761,7 +767,7 @@ __device__ __forceinline__ void point16_tile(const float* __restrict__ xyz, floa
         const int rr = r < 13 ? r : 12;
         float* rowp = rr == 0 ? s_v + size_t(j) * S
                               : (rr < 4 ? s_d + size_t(3 * j + rr - 1) * S : s_h + size_t(9 * j + rr - 4) * S);
-        point16_core<L, NORM>(x, y, z, r2, tb, lane, ir, rowp);
+        point16_core<L, NORM>(x, y, z, r2, tb, rr, lane & 16, ir, rowp, rowp, r < 13);
         if constexpr (MODE == 1) {
             if (bulk && r < 13 && j < cnt) {  // each lane sends the row it wrote
                 fence_proxy_async_smem();
@@ -822,6 +828,171 @@ __global__ void __launch_bounds__(128, 3) point16_fwd_kernel(const float* __rest
         const int64_t p0 = tile * P;
         const int cnt = int(min(int64_t(P), n - p0));
         point16_tile<L, NORM>(xyz, sph, dsph, ddsph, p0, cnt, P, bulk, buf, tb, lane);
+    }
+    if (bulk) bulk_wait_all();  // every lane: rows may leave by per-lane copies
+}
+
+// ------------------- forward with Hessians, 10 lanes per point (distinct planes)
+// POINT with lanes_per_point = 10 (FP32 values, gradients and Hessians): the
+// 30 first lanes of a warp compute 3 points per pass, lane 10j + r owning the
+// r-th distinct plane of point j (value, 3 gradient components, the Hessian
+// entries xx, xy, xz, yy, yz, zz; lanes 30, 31 idle). The lane of an
+// off-diagonal entry also writes its mirror, so no lane repeats another's
+// work: 1.6x the points per warp instruction of the 16-lane map. The planes
+// come from point16_core (the same role weights).
+//
+// Shared memory, odd K: the image of the tile's three global ranges, each
+// placed at its 16-byte phase so that the interior leaves by one bulk copy
+// per array (head and tail by plain stores). Even K (K % 4 == 0 in FP32):
+// every row is 16-byte aligned at both ends, so each lane keeps only its
+// distinct row (10 row slots per point at stride point4_stride) and sends it
+// by one bulk copy per global row, the mirror from the same slot.
+template <int L>
+__host__ __device__ constexpr size_t point10_warp_bytes(int P) {
+    constexpr int K = (L + 1) * (L + 1);
+    if constexpr (K % 2) {
+        const size_t v = (size_t(P) * K + 4 + 3) / 4 * 4, d = (size_t(3 * P) * K + 4 + 3) / 4 * 4,
+                     h = (size_t(9 * P) * K + 4 + 3) / 4 * 4;
+        return 4 * (v + d + h);
+    } else {
+        return size_t(4) * 10 * size_t(P) * size_t(point4_stride(L, 4));
+    }
+}
+
+__host__ __device__ constexpr int point10_plane(int r) {  // distinct plane r -> index among the 13
+    return r < 4 ? r : (r == 4 ? 4 : r == 5 ? 5 : r == 6 ? 6 : r == 7 ? 8 : r == 8 ? 9 : 12);
+}
+__host__ __device__ constexpr int point10_mirror(int q) {  // Hessian plane 4 + 3i + k -> 4 + 3k + i
+    return q < 4 ? q : 4 + 3 * ((q - 4) % 3) + (q - 4) / 3;
+}
+__host__ __device__ constexpr int point10_slot(int q) {  // plane among the 13 -> its distinct row
+    return q < 4 ? q : (q == 4 ? 4 : (q == 5 || q == 7) ? 5 : (q == 6 || q == 10) ? 6 : q == 8 ? 7 : (q == 9 || q == 11) ? 8 : 9);
+}
+
+// Sends elements [0, E) of a staged range (image element e at img[e], the
+// range's global start g; img and g share their 16-byte phase): the
+// 16-byte-aligned interior by one bulk copy from lane 0, the rest by plain
+// stores of the warp. Returns whether a bulk copy was issued.
+__device__ __forceinline__ bool point10_send(float* __restrict__ g, const float* __restrict__ img, int64_t E, int lane) {
+    const int64_t h = (4 - int64_t((reinterpret_cast<uintptr_t>(g) / 4) % 4)) % 4;
+    const int64_t nb = E > h ? (E - h) / 4 * 4 : 0;
+    if (nb > 0 && lane == 0) bulk_store(g + h, img + h, uint32_t(nb * 4));
+    for (int64_t i = lane; i < min(h, E); i += 32) g[i] = img[i];
+    for (int64_t i = h + nb + lane; i < E; i += 32) g[i] = img[i];
+    return nb > 0;
+}
+
+// One tile of P points (P a multiple of 3, <= 12): passes of 3 points.
+template <int L, bool NORM, typename Tabs>
+__device__ __forceinline__ void point10_tile(const float* __restrict__ xyz, float* __restrict__ sph,
+                                             float* __restrict__ dsph, float* __restrict__ ddsph, int64_t p0,
+                                             int cnt, int P, int bulk, unsigned char* buf, const Tabs& tb,
+                                             int lane) {
+    constexpr int K = (L + 1) * (L + 1);
+    constexpr bool IMG = (K % 2) != 0;
+    constexpr int S = IMG ? K : point4_stride(L, 4);
+    const int j = min(lane / 10, 2);
+    const int r = min(lane - 10 * j, 9);
+    const bool on = lane < 30;
+    const int rr = point10_plane(r), rm = point10_mirror(rr);
+    float *iv = nullptr, *id = nullptr, *ih = nullptr;
+    if constexpr (IMG) {
+        float* const sv = reinterpret_cast<float*>(buf);
+        float* const sd = sv + (size_t(P) * K + 4 + 3) / 4 * 4;
+        float* const sh = sd + (size_t(3 * P) * K + 4 + 3) / 4 * 4;
+        // each image shares the 16-byte phase of its global range
+        iv = sv + (bulk ? (reinterpret_cast<uintptr_t>(sph + p0 * K) / 4) % 4 : 0);
+        id = sd + (bulk ? (reinterpret_cast<uintptr_t>(dsph + p0 * 3 * K) / 4) % 4 : 0);
+        ih = sh + (bulk ? (reinterpret_cast<uintptr_t>(ddsph + p0 * 9 * K) / 4) % 4 : 0);
+    }
+    float* const slots = reinterpret_cast<float*>(buf);  // even K: 10 row slots per point
+    for (int t = 0; t < P; t += 3) {
+        const int pj = t + j;
+        const bool live = on && pj < cnt;
+        float x = 0.f, y = 0.f, z = 1.f;  // idle lanes run on a unit vector and store nothing
+        if (live) {
+            x = xyz[3 * (p0 + pj)];
+            y = xyz[3 * (p0 + pj) + 1];
+            z = xyz[3 * (p0 + pj) + 2];
+        }
+        float r2, ir = 1.f;
+        if (NORM) {
+            unit_point(x, y, z, r2, ir);
+        } else {
+            r2 = x * x + y * y + z * z;
+        }
+        if constexpr (IMG) {
+            float* rowp = rr == 0 ? iv + size_t(pj) * S
+                                  : (rr < 4 ? id + size_t(3 * pj + rr - 1) * S : ih + size_t(9 * pj + rr - 4) * S);
+            float* rowp2 = rr < 4 ? rowp : ih + size_t(9 * pj + rm - 4) * S;
+            point16_core<L, NORM, true>(x, y, z, r2, tb, rr, 10 * j, ir, rowp, rowp2, live);
+        } else {
+            float* rowp = slots + size_t(10 * pj + r) * S;
+            point16_core<L, NORM, false>(x, y, z, r2, tb, rr, 10 * j, ir, rowp, rowp, live);
+            if (bulk && live) {  // rows 16-byte aligned at both ends: one copy per global row
+                fence_proxy_async_smem();
+                const int64_t gp = p0 + pj;
+                float* g1 = rr == 0 ? sph + gp * K : (rr < 4 ? dsph + (gp * 3 + rr - 1) * K : ddsph + (gp * 9 + rr - 4) * K);
+                bulk_store(g1, rowp, uint32_t(K * 4));
+                if (rm != rr) bulk_store(ddsph + (gp * 9 + rm - 4) * K, rowp, uint32_t(K * 4));
+                bulk_commit();
+            }
+        }
+    }
+    if constexpr (!IMG) {
+        if (bulk) {
+            bulk_wait_read_all();
+            __syncwarp();
+            return;
+        }
+        // outputs not 16-byte aligned: the warp copies the 13 global rows of
+        // each point from their slots
+        __syncwarp();
+        for (int q = 0; q < 13 * cnt; ++q) {
+            const int pj = q / 13, pl = q - 13 * pj;
+            const int64_t gp = p0 + pj;
+            float* g = pl == 0 ? sph + gp * K : (pl < 4 ? dsph + (gp * 3 + pl - 1) * K : ddsph + (gp * 9 + pl - 4) * K);
+            const float* src = slots + size_t(10 * pj + point10_slot(pl)) * S;
+            for (int c = lane; c < K; c += 32) g[c] = src[c];
+        }
+        __syncwarp();
+        return;
+    } else {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (bulk) {
+            bool any = point10_send(sph + p0 * K, iv, int64_t(cnt) * K, lane);
+            any = point10_send(dsph + p0 * 3 * K, id, int64_t(3 * cnt) * K, lane) || any;
+            any = point10_send(ddsph + p0 * 9 * K, ih, int64_t(9 * cnt) * K, lane) || any;
+            if (lane == 0 && any) {
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+        } else {
+            for (int64_t i = lane; i < int64_t(cnt) * K; i += 32) sph[p0 * K + i] = iv[i];
+            for (int64_t i = lane; i < int64_t(3 * cnt) * K; i += 32) dsph[p0 * 3 * K + i] = id[i];
+            for (int64_t i = lane; i < int64_t(9 * cnt) * K; i += 32) ddsph[p0 * 9 * K + i] = ih[i];
+        }
+        __syncwarp();
+    }
+}
+
+template <int L, bool NORM>
+__global__ void __launch_bounds__(128, 3) point10_fwd_kernel(const float* __restrict__ xyz, int64_t n,
+                                                             const __grid_constant__ PointTabs<L, float, true> tb,
+                                                             float* __restrict__ sph, float* __restrict__ dsph,
+                                                             float* __restrict__ ddsph, int P, int bulk) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    unsigned char* buf = smem + size_t(warp) * point10_warp_bytes<L>(P);
+    const int64_t ntiles = (n + P - 1) / P;
+    const int64_t stride = int64_t(gridDim.x) * W;
+    for (int64_t tile = int64_t(blockIdx.x) * W + warp; tile < ntiles; tile += stride) {
+        const int64_t p0 = tile * P;
+        const int cnt = int(min(int64_t(P), n - p0));
+        point10_tile<L, NORM>(xyz, sph, dsph, ddsph, p0, cnt, P, bulk, buf, tb, lane);
     }
     if (bulk) bulk_wait_all();  // every lane: rows may leave by per-lane copies
 }
@@ -1159,6 +1330,26 @@ int launch_point16_fwd(const FwdArgs& a) {
     const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
     const size_t smem = size_t(W) * point16_warp_bytes<L>(P);
     auto kern = point16_fwd_kernel<L, NORM>;
+    cudaError_t err = ensure_smem(kern, smem);
+    if (err != cudaSuccess) return int(err);
+    const int64_t ntiles = ceil_div(a.n, P);
+    const int grid = grid_for(kern, 32 * W, smem, ntiles, a.launch.blocks_per_sm);
+    const bool bulk = reinterpret_cast<uintptr_t>(a.sph) % 16 == 0 && reinterpret_cast<uintptr_t>(a.dsph) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(a.ddsph) % 16 == 0;
+    kern<<<grid, 32 * W, smem, static_cast<cudaStream_t>(a.stream)>>>(
+        static_cast<const float*>(a.xyz), a.n, tb, static_cast<float*>(a.sph), static_cast<float*>(a.dsph),
+        static_cast<float*>(a.ddsph), P, bulk ? 1 : 0);
+    return int(cudaGetLastError());
+}
+
+// POINT forward with Hessians, 10 lanes per point (FP32); P (a multiple of 3,
+// <= 12) and W resolved by the caller.
+template <int L, bool NORM>
+int launch_point10_fwd(const FwdArgs& a) {
+    static const PointTabs<L, float, true> tb = make_point_tabs<L, float, true>();
+    const int P = a.launch.points_per_tile, W = a.launch.warps_per_block;
+    const size_t smem = size_t(W) * point10_warp_bytes<L>(P);
+    auto kern = point10_fwd_kernel<L, NORM>;
     cudaError_t err = ensure_smem(kern, smem);
     if (err != cudaSuccess) return int(err);
     const int64_t ntiles = ceil_div(a.n, P);

@@ -21,6 +21,10 @@ int SPH_CAT(point_fwd_L, SPH_INST_L)(const FwdArgs& a) {
                         : launch_point_fwd<L, true, false, false, T, TO>(a))    \
                 : (norm ? launch_point_fwd<L, false, false, true, T, TO>(a)     \
                         : launch_point_fwd<L, false, false, false, T, TO>(a));
+    if (a.launch.lanes_per_point == 10) {  // one lane per distinct plane, Hessians (FP32 arithmetic and storage)
+        if (a.ddsph == nullptr || a.dtype != SPH_F32 || a.out != SPH_OUT_SAME) return int(cudaErrorInvalidValue);
+        return norm ? launch_point10_fwd<L, true>(a) : launch_point10_fwd<L, false>(a);
+    }
     if (a.launch.lanes_per_point == 16) {  // one lane per output plane, Hessians (FP32 arithmetic and storage)
         if (a.ddsph == nullptr || a.dtype != SPH_F32 || a.out != SPH_OUT_SAME) return int(cudaErrorInvalidValue);
         return norm ? launch_point16_fwd<L, true>(a) : launch_point16_fwd<L, false>(a);

@@ -145,7 +145,8 @@ def test_host_downward_tables_reproduce_oracle():
 def test_auto_family_choice():
     """AUTO: DEGREE for FP64 arithmetic from l_max 14 (with gradients from
     9); ROW for FP32 arithmetic from POINT's range to l_max 63 and for FP32
-    Hessians from l_max 12; then SLICE (FP32 storage) or DEGREE (bf16
+    Hessians beyond it (scaled form; normalized from l_max 14); then SLICE
+    (FP32 storage) or DEGREE (bf16
     storage); FP64 Hessians on SLICE (host-only query)."""
     fam, shape = C.sphericart_launch_info(16, C.SPH_F64, C.SPH_OUT_SAME, 1, 0)
     assert fam == C.SPH_KERNEL_DEGREE and shape.lanes_per_point in (1, 2, 4)
@@ -156,6 +157,9 @@ def test_auto_family_choice():
     assert C.sphericart_launch_info(13, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_POINT
     assert C.sphericart_launch_info(14, C.SPH_F64, C.SPH_OUT_SAME, 0, 0)[0] == C.SPH_KERNEL_DEGREE
     assert C.sphericart_launch_info(20, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)[0] == C.SPH_KERNEL_ROW  # FP32 Hessians
+    assert C.sphericart_launch_info(17, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)[0] == C.SPH_KERNEL_ROW
+    fam, shape = C.sphericart_launch_info(16, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
+    assert fam == C.SPH_KERNEL_POINT and shape.lanes_per_point == 10
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_BF16, 1, 0)
     assert fam == C.SPH_KERNEL_ROW
     fam, _ = C.sphericart_launch_info(30, C.SPH_F32, C.SPH_OUT_SAME, 1, 0)

@@ -91,37 +91,3 @@ def test_launch_shapes_and_limits():
     with pytest.raises(C.SphericartError):  # FP64 arithmetic
         api.spherical_harmonics(x.double(), 9, False, gradients=True, hessians=True, kernel="point",
                                 launch=_sixteen())
-
-
-def test_auto_default():
-    """AUTO runs 16 lanes per point for FP32 Hessians where measured faster
-    (scaled l_max 8..10, normalized 9..11), the one-lane tile below, ROW from
-    l_max 12."""
-    fam, s = C.sphericart_launch_info(8, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
-    assert fam == C.SPH_KERNEL_POINT and s.lanes_per_point == 16
-    fam, s = C.sphericart_launch_info(6, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
-    assert s.lanes_per_point == 0
-    fam, s = C.sphericart_launch_info(8, C.SPH_F64, C.SPH_OUT_SAME, 1, 1)
-    assert s.lanes_per_point == 0
-    fam, s = C.sphericart_launch_info(12, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
-    assert fam == C.SPH_KERNEL_ROW
-    x = _t(inputs.shell_points(1000, 0.5, 2.0, seed=335))
-    for l_max, normalized in ((8, False), (10, True)):
-        a = api.spherical_harmonics(x, l_max, normalized, gradients=True, hessians=True)
-        b = api.spherical_harmonics(x, l_max, normalized, gradients=True, hessians=True, kernel="point",
-                                    launch=_sixteen())
-        assert all(torch.equal(u, w) for u, w in zip(a, b)), (l_max, normalized)
-
-
-def test_full_size_lmax8_every_point():
-    """400,000 points, l_max 8, scaled, FP32 Hessians on the AUTO path (16
-    lanes per point): every element of ddsph against the oracle, symmetric
-    planes bit for bit."""
-    import full_parity
-
-    n, l_max = 400_000, 8
-    x = inputs.shell_points(n, 0.5, 5.0, seed=336).astype(np.float32)
-    _, _, H = api.spherical_harmonics(_t(x), l_max, False, gradients=True, hessians=True)
-    eh, finite, sym = full_parity.hessian_errors(x.astype(np.float64), l_max, False, H.cpu().numpy())
-    assert finite and sym
-    assert np.all(eh <= 5e-6 * (np.arange(l_max + 1) + 1)), eh
