@@ -449,9 +449,14 @@ int sphericart_launch_info(int l_max, int dtype, int out, int grad, int hess,
 /* sphericart_set_launch: installs a tuned launch shape for forward calls with
  * this (l_max, dtype, out, grad) on the current device; used by AUTO/POINT
  * calls that pass launch == NULL (grad: 0 values, 1 + gradients, 2 + gradients
- * and Hessians). points_per_tile etc. are validated. */
+ * and Hessians). points_per_tile etc. are validated; lanes_per_point 0, 1, 4
+ * (FP32 gradients), 10 or 16 (FP32 Hessians, FP32 storage). */
 int sphericart_set_launch(int l_max, int dtype, int out, int grad,
                           const sph_launch* launch);
+
+/* sphericart_tune_clear: removes every tuned or installed POINT shape of the
+ * current device, so that later calls take the library defaults again. */
+int sphericart_tune_clear(void);
 
 /* ---------------------------------------------------------------- autotuner
  * sphericart_autotune: times every valid POINT forward launch shape (points

@@ -103,6 +103,7 @@ _PROTOS = {
     ),
     "sphericart_tune_export": (_I, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "sphericart_tune_import": (_I, [ctypes.c_char_p, ctypes.POINTER(_I)]),
+    "sphericart_tune_clear": (_I, []),
     "sphericart_fma_peak": (_I, [_I, _P, _I, ctypes.POINTER(ctypes.c_double)]),
 }
 
@@ -233,6 +234,10 @@ def sphericart_tune_import(text: str) -> int:
     k = ctypes.c_int(0)
     _call("sphericart_tune_import", text.encode(), ctypes.byref(k))
     return int(k.value)
+
+
+def sphericart_tune_clear():
+    return _call("sphericart_tune_clear")
 
 
 def sphericart_fma_peak(dtype, stream, reps=3) -> float:

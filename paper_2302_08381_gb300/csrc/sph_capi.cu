@@ -403,6 +403,35 @@ bool resolve_point(sph_launch& s, const sph_launch& dflt, int L, int elem, size_
     return true;
 }
 
+// Resolves the zero fields of a 10-lanes-per-point shape from the default and
+// validates it (message set on failure).
+bool resolve_point10(sph_launch& s, int L) {
+    const sph_launch d = default_point10_fwd(L);
+    if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = d.blocks_per_sm;
+    if (s.points_per_tile == 0) s.points_per_tile = d.points_per_tile;
+    if (s.warps_per_block == 0) s.warps_per_block = d.warps_per_block;
+    if (s.points_per_tile < 3 || s.points_per_tile > 12 || s.points_per_tile % 3 || s.warps_per_block < 1 ||
+        s.warps_per_block > 4 || s.blocks_per_sm < 0 || s.blocks_per_sm > 32) {
+        set_error("POINT with 10 lanes per point: points_per_tile 3, 6, 9 or 12, warps_per_block <= 4");
+        return false;
+    }
+    if (size_t(s.warps_per_block) * point10_tile_bytes(L, s.points_per_tile) > size_t(max_smem_optin())) {
+        set_error("POINT with 10 lanes per point: the tile does not fit shared memory");
+        return false;
+    }
+    return true;
+}
+
+// Resolves and validates a 16-lanes-per-point shape (message set on failure).
+bool resolve_point16(sph_launch& s, int L) {
+    if (!resolve_point(s, default_point16_fwd(L), L, 4, point16_row_bytes(L))) return false;
+    if (s.points_per_tile > 8 || s.points_per_tile % 2 || s.warps_per_block > 4) {
+        set_error("POINT with 16 lanes per point: points_per_tile even and <= 8, warps_per_block <= 4");
+        return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 sph_launch point_fwd_shape(int L, int grad) {
@@ -660,20 +689,8 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
                 set_error("POINT with 10 lanes per point takes FP32 arithmetic and storage with Hessians");
                 return SPH_EUNSUPPORTED;
             }
-            const sph_launch d10 = default_point10_fwd(l_max);
             sph_launch& s = a.launch;
-            if (s.points_per_tile == 0 && s.warps_per_block == 0 && s.blocks_per_sm == 0) s.blocks_per_sm = d10.blocks_per_sm;
-            if (s.points_per_tile == 0) s.points_per_tile = d10.points_per_tile;
-            if (s.warps_per_block == 0) s.warps_per_block = d10.warps_per_block;
-            if (s.points_per_tile < 3 || s.points_per_tile > 12 || s.points_per_tile % 3 || s.warps_per_block < 1 ||
-                s.warps_per_block > 4 || s.blocks_per_sm < 0 || s.blocks_per_sm > 32) {
-                set_error("POINT with 10 lanes per point: points_per_tile 3, 6, 9 or 12, warps_per_block <= 4");
-                return SPH_EINVAL;
-            }
-            if (size_t(s.warps_per_block) * point10_tile_bytes(l_max, s.points_per_tile) > size_t(max_smem_optin())) {
-                set_error("POINT with 10 lanes per point: the tile does not fit shared memory");
-                return SPH_EINVAL;
-            }
+            if (!resolve_point10(s, l_max)) return SPH_EINVAL;
             if (from_default) {
                 const int64_t tiles = (n + s.points_per_tile - 1) / s.points_per_tile;
                 const int64_t per_w = std::max<int64_t>(1, tiles / (2 * int64_t(sm_count())));
@@ -689,20 +706,16 @@ int sphericart_compute_ex(const void* xyz, int64_t n, int l_max, int normalized,
             set_error("POINT with 16 lanes per point takes FP32 arithmetic and storage with Hessians");
             return SPH_EUNSUPPORTED;
         }
-        const sph_launch dflt = lpp == 4    ? default_point4_fwd(l_max, eo)
-                                : lpp == 16 ? default_point16_fwd(l_max)
-                                            : default_point_fwd(l_max, grad, eo, hess);
-        const size_t row = lpp == 4 ? point4_row_bytes(l_max, eo)
-                           : lpp == 16 ? point16_row_bytes(l_max)
-                                       : point_row_bytes(l_max, grad, eo, hess);
-        if (!resolve_point(a.launch, dflt, l_max, eo, row)) return SPH_EINVAL;
-        if (lpp == 4 && a.launch.points_per_tile > 8) {
-            set_error("POINT with 4 lanes per point: points_per_tile must be <= 8 (32 lanes per warp)");
-            return SPH_EINVAL;
-        }
-        if (lpp == 16 && (a.launch.points_per_tile > 8 || a.launch.points_per_tile % 2 || a.launch.warps_per_block > 4)) {
-            set_error("POINT with 16 lanes per point: points_per_tile even and <= 8, warps_per_block <= 4");
-            return SPH_EINVAL;
+        if (lpp == 16) {
+            if (!resolve_point16(a.launch, l_max)) return SPH_EINVAL;
+        } else {
+            const sph_launch dflt = lpp == 4 ? default_point4_fwd(l_max, eo) : default_point_fwd(l_max, grad, eo, hess);
+            const size_t row = lpp == 4 ? point4_row_bytes(l_max, eo) : point_row_bytes(l_max, grad, eo, hess);
+            if (!resolve_point(a.launch, dflt, l_max, eo, row)) return SPH_EINVAL;
+            if (lpp == 4 && a.launch.points_per_tile > 8) {
+                set_error("POINT with 4 lanes per point: points_per_tile must be <= 8 (32 lanes per warp)");
+                return SPH_EINVAL;
+            }
         }
         if (from_default) {
             // Few tiles (small n): fewer warps per block, so that the blocks
@@ -953,11 +966,18 @@ int sphericart_set_launch(int l_max, int dtype, int out, int grad, const sph_lau
     const int eo = elem_size(dtype, out);
     const int g = grad >= 2 ? 2 : (grad ? 1 : 0);  // 2: values + gradients + Hessians
     sph_launch s = *launch;
-    if (s.lanes_per_point != 0 && s.lanes_per_point != 1 && s.lanes_per_point != 4) {
-        set_error("set_launch: POINT lanes_per_point must be 0, 1 or 4");
+    if (s.lanes_per_point != 0 && s.lanes_per_point != 1 && s.lanes_per_point != 4 && s.lanes_per_point != 10 &&
+        s.lanes_per_point != 16) {
+        set_error("set_launch: POINT lanes_per_point must be 0, 1, 4, 10 or 16");
         return SPH_EINVAL;
     }
-    if (s.lanes_per_point == 4) {
+    if (s.lanes_per_point == 10 || s.lanes_per_point == 16) {
+        if (g != 2 || dtype != SPH_F32 || out != SPH_OUT_SAME) {
+            set_error("set_launch: 10 or 16 lanes per point take FP32 arithmetic and storage with Hessians");
+            return SPH_EINVAL;
+        }
+        if (!(s.lanes_per_point == 10 ? resolve_point10(s, l_max) : resolve_point16(s, l_max))) return SPH_EINVAL;
+    } else if (s.lanes_per_point == 4) {
         if (g != 1 || dtype != SPH_F32) {
             set_error("set_launch: 4 lanes per point take FP32 arithmetic, values and gradients");
             return SPH_EINVAL;
@@ -976,6 +996,21 @@ int sphericart_set_launch(int l_max, int dtype, int out, int grad, const sph_lau
     cudaGetDevice(&d);
     std::lock_guard<std::mutex> lk(g_mu);
     g_tuned[TuneKey{d, l_max, dtype, out, g}] = s;
+    return SPH_OK;
+}
+
+int sphericart_tune_clear(void) {
+    int st = ensure_device("tune_clear");
+    if (st) return st;
+    int d = -1;
+    cudaGetDevice(&d);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_tuned.begin(); it != g_tuned.end();) {
+        if (std::get<0>(it->first) == d)
+            it = g_tuned.erase(it);
+        else
+            ++it;
+    }
     return SPH_OK;
 }
 

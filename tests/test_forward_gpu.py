@@ -110,8 +110,11 @@ def test_headline_lmax8_n4m_full():
     xyz = inputs.shell_points(n, 0.5, 5.0, seed=8)
     x = torch.from_numpy(xyz).to(DEV)
     api.autotune(x, l_max, False, True)  # installs the shape later calls use
-    sph, dsph = api.spherical_harmonics(x, l_max, gradients=True)
-    torch.cuda.synchronize()
+    try:
+        sph, dsph = api.spherical_harmonics(x, l_max, gradients=True)
+        torch.cuda.synchronize()
+    finally:
+        C.sphericart_tune_clear()  # process-wide: later tests see the defaults
     ev, eg, finite = full_parity.forward_errors(xyz.astype(np.float64), l_max, False,
                                                 sph.cpu().numpy(), dsph.cpu().numpy())
     assert finite

@@ -158,3 +158,32 @@ def test_full_size_lmax13_normalized_every_point():
     eh, finite, sym = full_parity.hessian_errors(x.astype(np.float64), l_max, True, H.cpu().numpy())
     assert finite and sym
     assert np.all(eh <= 5e-6 * (np.arange(l_max + 1) + 1)), eh
+
+
+def test_installed_shapes_and_clear():
+    """set_launch installs 10- and 16-lane Hessian shapes for AUTO calls
+    (validated like explicit launches); tune_clear restores the defaults."""
+    x = _t(inputs.shell_points(2000, 0.5, 2.0, seed=357))
+    L = 9
+    ref = api.spherical_harmonics(x, L, False, gradients=True, hessians=True, kernel="point", launch=_ten(3, 1))
+    try:
+        C.sphericart_set_launch(L, C.SPH_F32, C.SPH_OUT_SAME, 2, _ten(6, 2, 0))
+        fam, s = C.sphericart_launch_info(L, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
+        assert fam == C.SPH_KERNEL_POINT and (s.points_per_tile, s.warps_per_block, s.lanes_per_point) == (6, 2, 10)
+        out = api.spherical_harmonics(x, L, False, gradients=True, hessians=True)
+        assert all(torch.equal(u, w) for u, w in zip(ref, out))
+        C.sphericart_set_launch(L, C.SPH_F32, C.SPH_OUT_SAME, 2, C.make_launch(4, 1, 0, 16))
+        fam, s = C.sphericart_launch_info(L, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
+        assert s.lanes_per_point == 16
+        out = api.spherical_harmonics(x, L, False, gradients=True, hessians=True)
+        for u, w in zip(ref, out):
+            assert (u - w).abs().max().item() <= 2e-6 * max(1.0, u.abs().max().item())
+        for grad, lau in ((1, _ten()), (2, _ten(4, 1)), (2, _ten(6, 5)), (2, C.make_launch(3, 1, 0, 16))):
+            with pytest.raises(C.SphericartError):
+                C.sphericart_set_launch(L, C.SPH_F32, C.SPH_OUT_SAME, grad, lau)
+        with pytest.raises(C.SphericartError):  # FP64
+            C.sphericart_set_launch(L, C.SPH_F64, C.SPH_OUT_SAME, 2, _ten())
+    finally:
+        C.sphericart_tune_clear()
+    fam, s = C.sphericart_launch_info(L, C.SPH_F32, C.SPH_OUT_SAME, 1, 1)
+    assert (s.points_per_tile, s.lanes_per_point) == (3, 10)

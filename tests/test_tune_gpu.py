@@ -12,6 +12,14 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
+@pytest.fixture(autouse=True)
+def _restore_defaults():
+    """Tuned shapes are process-wide: drop them after each test, so that later
+    tests see the library defaults whatever the test order."""
+    yield
+    C.sphericart_tune_clear()
+
+
 def test_autotune_installs_a_valid_shape_with_identical_results():
     n, L = 200_003, 8
     x = torch.from_numpy(inputs.shell_points(n, 0.5, 5.0, seed=400)).to(DEV)
