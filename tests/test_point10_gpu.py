@@ -61,9 +61,11 @@ def test_matches_sixteen_lanes():
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 7, 13])
 def test_edge_sizes_phases_and_bounds(n):
-    """Outputs that start at each of the four 4-byte offsets within 16 bytes
-    (odd K: bulk interior, plain head and tail; even K: plain copy-out when a
-    row is not 16-byte aligned); guard elements on both sides untouched."""
+    """Outputs that start at each of the four 4-byte offsets within 16 bytes:
+    bulk copies need all three arrays 16-byte aligned, so these take the
+    warp's plain copy-out (the bulk image at every 16-byte phase of a tile
+    start is covered by 3-point tiles of odd K below, checked bit for bit
+    against 6-point tiles); guard elements on both sides untouched."""
     for l_max in (0, 1, 2, 3, 8, 9):
         K = (l_max + 1) ** 2
         x = inputs.normal_points(max(n, 1), seed=353)[:n].astype(np.float32)
